@@ -1,0 +1,316 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each ``check_*`` takes an oracle build and raises AssertionError when it does
+not agree with what the paper and the mathematics fix:
+
+* exact rational arithmetic (sympy) on the fixed covariance of the plain
+  workload;
+* numpy.linalg (LAPACK: LU inverse, LU determinant, Hermitian eigenvalues) on
+  random matrices, an independent library route;
+* Z Z^-1 = I, a Hermitian inverse, a real positive determinant equal to the
+  product of the eigenvalues, agreement of all row and column cofactor
+  expansions (§3.1), det(Z^-1) = 1/det Z, Hadamard det <= a d f;
+* the closed forms of diagonal, block-diagonal (§5) and scalar Z, and of
+  U diag(l) U^H with known l;
+* brute-force Python loops for the window covariance (Eq. ZN);
+* central finite differences through numpy.linalg for the gradients;
+* q <= 0, q(Z, Z) = 0, Euler homogeneity and date-swap symmetry for the Wishart
+  change statistic.
+
+``test_mutants_are_caught`` builds the oracle with each planted mistake and
+requires that at least one check fails for each.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from helpers import pack, random_pd, unpack
+
+import oracle
+from paper_1807_08084_gb300 import synth
+
+
+# --------------------------------------------------------------------------
+# the checks
+# --------------------------------------------------------------------------
+def check_sigma_exact(o):
+    """Fixed Sigma of the plain workload vs exact rational arithmetic."""
+    sympy = pytest.importorskip("sympy")
+    R, Ii = sympy.Rational, sympy.I
+    b = R(3, 10) + R(1, 10) * Ii
+    c = R(1, 2)
+    e = R(1, 20) * Ii
+    S = sympy.Matrix([[1, b, c], [sympy.conjugate(b), R(2, 5), e],
+                      [sympy.conjugate(c), sympy.conjugate(e), R(9, 10)]])
+    det_exact = S.det()
+    inv_exact = S.inv()
+    assert det_exact == R(13, 80)
+    z = pack(synth.SIGMA_FIXED[None])
+    zinv, det, det_im = o.zinv_det(z, with_imag=True)
+    assert abs(det[0] - 13 / 80) <= 1e-15 * 13 / 80 * 50
+    assert abs(det_im[0]) <= 1e-16
+    ref = pack(np.array(inv_exact.evalf(30).tolist(), dtype=np.complex128)[None])
+    np.testing.assert_allclose(zinv[:, 0], ref[:, 0], rtol=0, atol=1e-13)
+    lam = o.eigvals(z)[:, 0]
+    # characteristic-polynomial invariants: trace, sum of principal 2x2 minors, det
+    tr = float(sympy.re(S.trace()))
+    m2 = float(sympy.re(sum(S.extract([i, j], [i, j]).det()
+                           for i, j in itertools.combinations(range(3), 2))))
+    assert abs(lam.sum() - tr) < 1e-13
+    assert abs(lam[0] * lam[1] + lam[0] * lam[2] + lam[1] * lam[2] - m2) < 1e-13
+    assert abs(lam.prod() - 13 / 80) < 1e-13
+
+
+def check_random_vs_numpy(o):
+    rng = np.random.default_rng(11)
+    A = random_pd(rng, 2000, cond_max=1e4)
+    z = pack(A)
+    zinv, det = o.zinv_det(z)
+    ref_inv = np.linalg.inv(A)
+    ref_det = np.linalg.det(A).real
+    lam_ref = np.linalg.eigvalsh(A)
+    cond = lam_ref[:, 2] / lam_ref[:, 0]
+    np.testing.assert_array_less(np.abs(det - ref_det) / ref_det, 1e-13 * cond)
+    scale = np.abs(pack(ref_inv)).max(axis=0)
+    np.testing.assert_array_less(np.abs(zinv - pack(ref_inv)).max(axis=0) / scale, 1e-13 * cond)
+    lam = o.eigvals(z)
+    np.testing.assert_array_less(np.abs(lam - lam_ref.T).max(axis=0) / lam_ref[:, 2], 1e-13)
+
+
+def check_identity_and_hermitian(o):
+    rng = np.random.default_rng(12)
+    z = pack(random_pd(rng, 1000, cond_max=1e5))
+    A = unpack(z)  # exactly Hermitian
+    zinv, _ = o.zinv_det(z)
+    W = unpack(zinv)
+    lam = np.linalg.eigvalsh(A)
+    cond = lam[:, 2] / lam[:, 0]
+    err = np.abs(A @ W - np.eye(3)).max(axis=(1, 2))
+    np.testing.assert_array_less(err, 1e-12 * cond)
+    X = o.inverse_full(z, "ge")
+    herm = np.abs(X - np.conj(np.transpose(X, (0, 2, 1)))).max(axis=(1, 2))
+    np.testing.assert_array_less(herm / np.abs(X).max(axis=(1, 2)), 1e-13 * cond)
+    # the packed output is the upper triangle of the full inverse
+    np.testing.assert_allclose(pack(X), zinv, rtol=0, atol=0)
+    # two derivations of the inverse agree (GE vs adj/det, Eq. inv_adjoint)
+    Y = o.inverse_full(z, "adj")
+    np.testing.assert_array_less(np.abs(X - Y).max(axis=(1, 2)) / np.abs(X).max(axis=(1, 2)),
+                                 1e-13 * cond)
+
+
+def check_det_properties(o):
+    rng = np.random.default_rng(13)
+    A = random_pd(rng, 1000, cond_max=1e3)
+    z = pack(A)
+    _, det, det_im = o.zinv_det(z, with_imag=True)
+    assert np.all(det > 0)
+    lam_np = np.linalg.eigvalsh(unpack(z))
+    cond = lam_np[:, 2] / lam_np[:, 0]
+    # det is real (§3.1): the imaginary part is rounding, relative to the terms' size
+    np.testing.assert_array_less(np.abs(det_im) / det, 1e-14 * cond)
+    ex = o.det_expansions(z)  # six expansions (§3.1: any row or column)
+    np.testing.assert_array_less(np.abs(ex - det).max(axis=0) / det, 1e-13 * cond)
+    lam = o.eigvals(z)
+    np.testing.assert_array_less(np.abs(lam.prod(axis=0) - det) / det, 1e-13 * cond)
+    # det(Z^-1) = 1 / det Z
+    zinv, _ = o.zinv_det(z)
+    dW = np.linalg.det(unpack(zinv)).real
+    np.testing.assert_array_less(np.abs(dW * det - 1), 1e-13 * cond)
+    # Hadamard: det <= a d f for PD
+    assert np.all(det <= z[0] * z[5] * z[8] * (1 + 1e-14))
+
+
+def check_closed_forms(o):
+    rng = np.random.default_rng(14)
+    n = 200
+    # diagonal: W = diag(1/a, 1/d, 1/f), det = a d f
+    a, d, f = (rng.uniform(0.01, 10, n) for _ in range(3))
+    z = np.zeros((9, n))
+    z[0], z[5], z[8] = a, d, f
+    zinv, det = o.zinv_det(z)
+    np.testing.assert_allclose(det, a * d * f, rtol=1e-15)
+    np.testing.assert_allclose(zinv[[0, 5, 8]], np.stack([1 / a, 1 / d, 1 / f]), rtol=1e-15)
+    assert np.all(zinv[[1, 2, 3, 4, 6, 7]] == 0)
+    # block-diagonal (b = c = 0, §5): det = a (d f - |e|^2), blockwise inverse
+    e = (rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)) * np.sqrt(d * f) * 0.9
+    z = np.zeros((9, n))
+    z[0], z[5], z[8], z[6], z[7] = a, d, f, e.real, e.imag
+    zinv, det = o.zinv_det(z)
+    m = d * f - np.abs(e) ** 2
+    np.testing.assert_allclose(det, a * m, rtol=1e-12)
+    np.testing.assert_allclose(zinv[0], 1 / a, rtol=1e-14)
+    np.testing.assert_allclose(zinv[5], f / m, rtol=1e-11)
+    np.testing.assert_allclose(zinv[8], d / m, rtol=1e-11)
+    np.testing.assert_allclose(zinv[6] + 1j * zinv[7], -e / m, rtol=1e-11)
+    assert np.all(np.abs(zinv[[1, 2, 3, 4]]) <= 1e-15 * np.abs(zinv[0]))
+    # scalar c I
+    c = rng.uniform(0.01, 100, n)
+    z = np.zeros((9, n))
+    z[0] = z[5] = z[8] = c
+    zinv, det = o.zinv_det(z)
+    np.testing.assert_allclose(det, c ** 3, rtol=1e-15)
+    np.testing.assert_allclose(zinv[[0, 5, 8]], np.stack([1 / c] * 3), rtol=1e-15)
+    # Z = U diag(l) U^H with known l: spectrum, det, cond, inverse
+    G = rng.standard_normal((n, 3, 3)) + 1j * rng.standard_normal((n, 3, 3))
+    U, _ = np.linalg.qr(G)
+    lam = np.sort(np.exp(rng.uniform(np.log(1e-2), np.log(1e2), (n, 3))), axis=1)
+    A = (U * lam[:, None, :]) @ np.conj(np.transpose(U, (0, 2, 1)))
+    z = pack(A)
+    np.testing.assert_allclose(o.eigvals(z), lam.T, rtol=1e-11)
+    np.testing.assert_allclose(o.cond(z), lam[:, 2] / lam[:, 0], rtol=1e-10)
+    zinv, det = o.zinv_det(z)
+    np.testing.assert_allclose(det, lam.prod(axis=1), rtol=1e-11)
+    Winv = (U / lam[:, None, :]) @ np.conj(np.transpose(U, (0, 2, 1)))
+    np.testing.assert_allclose(zinv, pack(Winv), rtol=0, atol=1e-10 * np.abs(pack(Winv)).max())
+
+
+def _brute_window(s, win, w):
+    """Window covariance by explicit loops (clamp-to-edge addressing)."""
+    _, H, W = s.shape
+    r = (win - 1) // 2
+    out = np.zeros((H * W, 3, 3), dtype=np.complex128)
+    for y in range(H):
+        for x in range(W):
+            acc = np.zeros((3, 3), dtype=np.complex128)
+            for dy in range(-r, r + 1):
+                for dx in range(-r, r + 1):
+                    yy = min(max(y + dy, 0), H - 1)
+                    xx = min(max(x + dx, 0), W - 1)
+                    v = s[:, yy, xx].astype(np.complex128)
+                    wk = 1.0 / (win * win) if w is None else float(w[(dy + r) * win + dx + r])
+                    for i in range(3):
+                        for j in range(3):
+                            acc[i, j] += wk * v[i] * np.conj(v[j])
+            out[y * W + x] = acc
+    return out
+
+
+def check_multilook_brute(o):
+    rng = np.random.default_rng(15)
+    s = (rng.standard_normal((3, 6, 7)) + 1j * rng.standard_normal((3, 6, 7))).astype(np.complex64)
+    for win in (1, 3, 5):
+        ref = pack(_brute_window(s, win, None))
+        np.testing.assert_allclose(o.multilook(s, win), ref, rtol=1e-13, atol=1e-14)
+    w = rng.uniform(0.1, 1.0, 9).astype(np.float32)
+    ref = pack(_brute_window(s, 3, w))
+    np.testing.assert_allclose(o.multilook(s, 3, w), ref, rtol=1e-13, atol=1e-14)
+    # a constant image gives the rank-one S S^H everywhere (boxcar mean, Eq. ZN)
+    c = np.broadcast_to(s[:, :1, :1], s.shape).copy()
+    v = s[:, 0, 0].astype(np.complex128)
+    ref = pack(np.outer(v, np.conj(v))[None])
+    np.testing.assert_allclose(o.multilook(c, 5), np.repeat(ref, 42, axis=1), rtol=1e-13,
+                               atol=1e-14)
+
+
+def _loss_numpy(z, gW, gdet, glog):
+    A = unpack(z)
+    W = pack(np.linalg.inv(A))
+    det = np.linalg.det(A).real
+    return np.sum(gW * W) + np.sum(gdet * det) + np.sum(glog * np.log(det))
+
+
+def check_bwd_finite_differences(o):
+    rng = np.random.default_rng(16)
+    n = 40
+    z = pack(random_pd(rng, n, cond_max=30))
+    gW = rng.uniform(-1, 1, (9, n))
+    gdet = rng.uniform(-1, 1, n)
+    glog = rng.uniform(-1, 1, n)
+    for args in ((gW, None, None), (None, gdet, None), (None, None, glog), (gW, gdet, glog)):
+        g = o.zinv_det_bwd(z, *args)
+        a = [np.zeros((9, n)) if args[0] is None else args[0],
+             np.zeros(n) if args[1] is None else args[1],
+             np.zeros(n) if args[2] is None else args[2]]
+        fd = np.empty((9, n))
+        for k in range(9):
+            h = 1e-6 * np.abs(z).max(axis=0)
+            for p in range(n):
+                zp, zm = z.copy(), z.copy()
+                zp[k, p] += h[p]
+                zm[k, p] -= h[p]
+                sel = (slice(None), slice(p, p + 1))
+                fd[k, p] = (_loss_numpy(zp[sel], a[0][sel], a[1][p:p + 1], a[2][p:p + 1])
+                            - _loss_numpy(zm[sel], a[0][sel], a[1][p:p + 1], a[2][p:p + 1])) / (2 * h[p])
+        scale = np.abs(fd).max(axis=0) + 1e-30
+        np.testing.assert_array_less(np.abs(g - fd).max(axis=0) / scale, 1e-6)
+
+
+def _wishart_numpy(s1, s2, win, w):
+    Z1 = _brute_window(s1, win, w)
+    Z2 = _brute_window(s2, win, w)
+    l1 = np.linalg.slogdet(Z1)[1]
+    l2 = np.linalg.slogdet(Z2)[1]
+    lm = np.linalg.slogdet((Z1 + Z2) / 2)[1]
+    return l1 + l2 - 2 * lm
+
+
+def check_wishart(o):
+    rng = np.random.default_rng(17)
+    H, W, win = 5, 6, 3
+    s1 = (rng.standard_normal((3, H, W)) + 1j * rng.standard_normal((3, H, W))).astype(np.complex64)
+    s2 = (rng.standard_normal((3, H, W)) + 1j * rng.standard_normal((3, H, W))).astype(np.complex64)
+    w = rng.uniform(0.5, 1.5, win * win)
+    loss, q = o.wishart_fwd(s1, s2, win, w, want_map=True)
+    qref = _wishart_numpy(s1, s2, win, w)
+    np.testing.assert_allclose(q, qref, rtol=1e-10, atol=1e-11)
+    assert abs(loss - qref.sum()) < 1e-10 * max(1, abs(loss))
+    assert np.all(q <= 1e-12)
+    # no change: q = 0
+    l0, q0 = o.wishart_fwd(s1, s1, win, w, want_map=True)
+    assert np.all(np.abs(q0) < 1e-12)
+    # swapping the dates leaves L and its gradient unchanged
+    assert abs(o.wishart_fwd(s2, s1, win, w) - loss) < 1e-12 * abs(loss)
+    g = o.wishart_bwd(s1, s2, win, w, 1.0)
+    np.testing.assert_allclose(o.wishart_bwd(s2, s1, win, w, 1.0), g, rtol=1e-10, atol=1e-12)
+    # Euler: L is homogeneous of degree 0 in w
+    assert abs(np.dot(w, g)) < 1e-9 * np.abs(g).max() * np.abs(w).max()
+    # central finite differences through numpy
+    fd = np.empty(win * win)
+    for k in range(win * win):
+        h = 1e-6 * max(1.0, abs(w[k]))
+        wp, wm = w.copy(), w.copy()
+        wp[k] += h
+        wm[k] -= h
+        fd[k] = (_wishart_numpy(s1, s2, win, wp).sum() - _wishart_numpy(s1, s2, win, wm).sum()) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
+    # upstream scalar
+    np.testing.assert_allclose(o.wishart_bwd(s1, s2, win, w, -2.5), -2.5 * g, rtol=1e-14)
+
+
+CHECKS = [check_sigma_exact, check_random_vs_numpy, check_identity_and_hermitian,
+          check_det_properties, check_closed_forms, check_multilook_brute,
+          check_bwd_finite_differences, check_wishart]
+
+
+@pytest.mark.parametrize("check", CHECKS, ids=lambda c: c.__name__)
+def test_oracle_pin(orc, check):
+    check(orc)
+
+
+# mutant id -> what it plants (see ORACLE_MUTANT in oracle.c)
+MUTANTS = {
+    1: "cofactor sign ignores the column",
+    2: "lower triangle not conjugated on unpack",
+    3: "packs the lower triangle of the inverse",
+    4: "window covariance drops the conjugate",
+    5: "wrong clamp bound at the bottom edge",
+    6: "packed gradient drops the factor 2",
+    7: "Wishart statistic drops the 1/2 in the pooled matrix",
+    8: "Wishart gradient drops the factor 2 on W_12",
+    9: "Jacobi rotation loses the sign of tau",
+    10: "gradient sign of the W G W term",
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS), ids=lambda m: f"m{m}")
+def test_mutants_are_caught(mutant):
+    o = oracle.load(mutant=mutant)
+    failed = []
+    for check in CHECKS:
+        try:
+            with np.errstate(all="ignore"):
+                check(o)
+        except (AssertionError, FloatingPointError, ValueError):
+            failed.append(check.__name__)
+    assert failed, f"no pin catches mutant {mutant}: {MUTANTS[mutant]}"
