@@ -1,0 +1,363 @@
+"""Throughput of the per-pixel 3x3 Hermitian inverse + determinant on a GB300.
+
+Workload (default): the 16384 x 16384 packed-FP32 image (268,435,456 matrices,
+N = 16 looks, 8 class covariances in 512 x 512 blocks), generated on the GPU
+from the seeded generator.  One step = one launch of zinv_det (Alg. 2 of the
+paper, plain FP32) over the whole image: 36 B read and 40 B written per matrix,
+20.4 GB per step, so every step streams well past the 126 MB L2.
+
+The JSON line carries the headline (adjugate Gmatrices/s), the same launch for
+the Cholesky baseline (Alg. 1), the compensated and FP64-recompute variants,
+the backward, the end-to-end number through the host-buffer entry point, the
+roofline of the dominant kernel, the FP64 oracle timed on the host cores, and
+the SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank runs the same per-GPU workload on its own
+synthetic image (weak scaling, no data-path collective); the time is the max
+over ranks and the value the matrices of all ranks over that time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+import torch
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "Gmatrices/s and HBM GB/s (% of peak) for 3x3 inv+det: adjugate vs Cholesky; fwd+bwd"
+UNIT = "Gmatrices/s"
+BYTES_FWD = 76     # 9 planes in + 9 planes + det out, FP32
+BYTES_BWD = 116    # W, det, g_W, g_det in; g_Z out
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_1807_08084_gb300" / "csrc").glob("*")):
+        if f.suffix in (".cu", ".cuh"):
+            h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on this source."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text()).get(kernel)
+    if not d or d.get("source_hash") != kernel_source_hash():
+        return None
+    return float(d["bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.samples = []
+        self.proc = None
+        uuid = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+        except Exception:
+            pass
+        self.target = (["-i", uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"]
+                       if uuid else ["-i", str(device_index)])
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", *self.target, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except FileNotFoundError:
+            self.proc = None
+            return
+        self.t0 = time.time()
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        return self.summary()
+
+    def summary(self, t_from=None, t_to=None):
+        rows = []
+        for t, line in self.samples:
+            if t_from is not None and not (t_from <= t <= t_to):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed(fn, steps: int, warmup: int, world: int) -> float:
+    """Average ms per call: CUDA events on the launching stream, barrier and
+    synchronize on both sides, max over ranks."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier(world)
+    return max_over_ranks(e0.elapsed_time(e1) / steps, world)
+
+
+def cpu_oracle_baseline(z_dev: torch.Tensor, budget_s: float = 12.0):
+    """The FP64 oracle on the host cores, on the first pixels of the same image,
+    chunk after chunk until ~budget_s of oracle time."""
+    import oracle
+    o = oracle.load()
+    zf = z_dev.reshape(9, -1)
+    chunk = 1 << 21
+    done, spent, p0 = 0, 0.0, 0
+    while spent < budget_s and p0 < zf.shape[1]:
+        zc = zf[:, p0:p0 + chunk].cpu().numpy()
+        t = time.perf_counter()
+        o.zinv_det(zc)
+        spent += time.perf_counter() - t
+        done += zc.shape[1]
+        p0 += chunk
+    return {"value": done / spent / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} matrices of the same image, FP64 cofactor det + "
+                      f"Gauss-Jordan inverse, single thread ({spent:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    """The FP64 oracle timed on the host cores (the reference arm)."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1807_08084_gb300 import synth as S
+    w = S.WORKLOADS["scale_16k"]
+    o = oracle.load()
+    m = 1 << 18
+    z = w.packed_z(np.arange(m, dtype=np.uint64))   # numpy twin, CPU only
+    for _ in range(args.warmup):
+        o.zinv_det(z)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.zinv_det(z)
+    dt = (time.perf_counter() - t) / args.steps
+    value = m / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{w.name}: first {m} of 16384x16384 packed Z, N=16 looks, "
+                                   "8 classes in 512x512 blocks (bounded CPU sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{m} matrices per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sub-steps", type=int, default=50, help="steps per secondary path")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import paper_1807_08084_gb300 as zp
+    from paper_1807_08084_gb300 import synth as S
+    from paper_1807_08084_gb300.synth import gpu as G
+
+    zp.load()
+    w = S.WORKLOADS["scale_16k"]
+    if world > 1:
+        from dataclasses import replace
+        w = replace(w, seed=w.seed + 1000 * rank)
+    n = w.n
+    z = G.packed_z(w)
+    zinv = torch.empty_like(z)
+    det = torch.empty((w.H, w.W), device="cuda")
+    hbm_peak, peak_kind = peaks()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    # --- headline: adjugate (Alg. 2), plain FP32 -----------------------------
+    t_from = time.time()
+    ms = timed(lambda: zp.zinv_det(z, zp.PLAIN, out=(zinv, det)), args.steps, args.warmup, world)
+    t_to = time.time()
+    clocks = sampler.summary(t_from, t_to)
+
+    def path(ms_):
+        gbs = BYTES_FWD * n / (ms_ * 1e-3) / 1e9
+        return {"gmat_s": n / (ms_ * 1e-3) / 1e9, "ms": ms_, "gbs": gbs,
+                "frac_hbm": gbs / hbm_peak}
+
+    paths = {"adjugate": path(ms)}
+    sub = args.sub_steps
+    paths["cholesky"] = path(timed(lambda: zp.chol_zinv_det(z, out=(zinv, det)), sub,
+                                   args.warmup, world))
+    paths["compensated"] = path(timed(lambda: zp.zinv_det(z, zp.COMPENSATED, out=(zinv, det)),
+                                      sub, args.warmup, world))
+    counts = zp.zinv_det(z, zp.FP64_RECOMPUTE, want_counts=True, out=(zinv, det))[2]
+    paths["fp64_recompute"] = path(timed(
+        lambda: zp.zinv_det(z, zp.FP64_RECOMPUTE, out=(zinv, det)), sub, args.warmup, world))
+    paths["fp64_recompute"]["flagged_fraction"] = int(counts[1]) / n
+    paths["compensated_fp64"] = path(timed(
+        lambda: zp.zinv_det(z, zp.COMPENSATED | zp.FP64_RECOMPUTE, out=(zinv, det)), sub,
+        args.warmup, world))
+    # backward from saved (W, det) with upstream gradients of W and det
+    zp.zinv_det(z, zp.PLAIN, out=(zinv, det))
+    g_w = G.uniform(w.seed, 9 * n, stream=1).reshape(9, w.H, w.W)
+    g_det = G.uniform(w.seed, n, stream=2).reshape(w.H, w.W)
+    g_z = torch.empty_like(z)
+    ms_bwd = timed(lambda: zp.zinv_det_bwd(zinv, det, g_w, g_det, None, out=g_z), sub,
+                   args.warmup, world)
+    gbs_bwd = BYTES_BWD * n / (ms_bwd * 1e-3) / 1e9
+    paths["backward"] = {"gmat_s": n / (ms_bwd * 1e-3) / 1e9, "ms": ms_bwd, "gbs": gbs_bwd,
+                         "frac_hbm": gbs_bwd / hbm_peak}
+    paths["fwd_plus_bwd"] = {"gmat_s": n / ((ms + ms_bwd) * 1e-3) / 1e9, "ms": ms + ms_bwd}
+    del g_w, g_det, g_z
+    sampler.stop()
+
+    # --- end to end through the host-buffer entry point -----------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        z_host = torch.empty(z.shape, dtype=torch.float32, pin_memory=True)
+        z_host.copy_(z)
+        zinv_h = torch.empty(z.shape, dtype=torch.float32, pin_memory=True)
+        det_h = torch.empty((w.H, w.W), dtype=torch.float32, pin_memory=True)
+        chunk = 1 << 24
+        ws = torch.empty(zp.zinv_det_host_workspace_bytes(chunk), dtype=torch.uint8,
+                         device="cuda")
+        ms_e2e = timed(lambda: zp.zinv_det_host(z_host, ws, zp.PLAIN, out=(zinv_h, det_h)),
+                       args.e2e_steps, 1, world)
+        e2e = {"value": world * n / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 36 * n, "d2h_bytes_per_step": 40 * n,
+               "ms_per_step": ms_e2e, "api": "zinv_det_host (pinned host buffers, chunked "
+                                             f"{chunk} matrices, 3 streams)"}
+        del z_host, zinv_h, det_h, ws
+
+    cpu = cpu_oracle_baseline(z) if (rank == 0 and world == 1) else None
+    traffic = traffic_record("zinv_det_plain_vec4")
+    achieved = BYTES_FWD * n / (ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "scale_16k: 16384x16384 packed FP32 Hermitian Z "
+                                   "(268,435,456 matrices), N=16 looks, 8 class covariances "
+                                   "in 512x512 blocks",
+                       "matrices_per_gpu": n, "bytes_per_step_per_gpu": BYTES_FWD * n,
+                       "l2": "inputs larger than L2 (20.4 GB streamed per step)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_inv_det_vec4<plain>",
+                         "algorithmic_bytes_per_launch": BYTES_FWD * n},
+            "paths": paths,
+            "speedup_vs_cholesky": paths["cholesky"]["ms"] / ms,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * zinv.h -- C ABI of libzinv.so: inverse and determinant of every pixel's 3x3
+ * Hermitian positive-definite PolSAR covariance matrix on a GB300 (sm_103a).
+ *
+ * Method: D. F. G. Coelho, R. J. Cintra, A. C. Frery, V. S. Dimitrov, "Fast
+ * Matrix Inversion and Determinant Computation for Polarimetric Synthetic
+ * Aperture Radar", arXiv:1807.08084.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Packed Hermitian layout (§2.1: only the upper triangle is stored).  A pixel's
+ *     Z = [[a, b, c], [conj b, d, e], [conj c, conj e, f]],  a, d, f real,
+ * is stored as nine float planes in the paper's letter order
+ *     plane 0:a 1:Re b 2:Im b 3:Re c 4:Im c 5:d 6:Re e 7:Im e 8:f
+ * and element k of pixel p lives at ptr[k*ld + p] (ld >= n, in elements).  A
+ * torch tensor of shape [9, H, W] (contiguous) is this layout with ld = H*W.
+ * Outputs Z^-1 use the same layout; det is one float plane [n].
+ *
+ * Single-look data (§1: S = [S_HH, S_HV, S_VV]^T): three complex64 planes,
+ * interleaved (re, im) floats; component i of pixel (y, x) at s[i*plane_ld + y*W + x]
+ * (plane_ld and the index in complex elements).
+ *
+ * Memory: every pointer is owned by the caller.  Unless an entry point says
+ * otherwise, pointers are device pointers (cudaMalloc, torch) or managed
+ * memory; the library allocates no device memory in any call and keeps no
+ * reference after the call returns.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Every call enqueues its work asynchronously on that stream and
+ * returns without synchronizing; results are valid once the stream reaches
+ * that point.
+ *
+ * Errors: every int-returning call returns ZINV_OK (0) or a negative code.  An
+ * argument error is detected on the host before anything is enqueued.  Nothing
+ * in the library traps or asserts on the device; per-pixel problems (a matrix
+ * that is not positive definite, non-finite input) are reported in the
+ * optional status plane and counters and leave IEEE results in the outputs.
+ * Calls that share output buffers and overlap on the GPU race; nothing else is
+ * shared between calls, except the streams zinv_det_host keeps per device.
+ */
+#ifndef ZINV_H
+#define ZINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZINV_ABI_VERSION 1
+
+/* return codes */
+#define ZINV_OK 0
+#define ZINV_ERR_ARG (-1)    /* null/misaligned/inaccessible pointer, bad size or flag */
+#define ZINV_ERR_LAUNCH (-2) /* a CUDA call or kernel launch failed */
+#define ZINV_ERR_DEVICE (-3) /* current device is not an sm_103 GPU, or no device */
+
+/* flags of zinv_det / multilook_zinv_det / zinv_det_host (bitwise or) */
+#define ZINV_PLAIN 0u
+#define ZINV_COMPENSATED 1u   /* FMA error-free products and sums in the cofactors and det */
+#define ZINV_FP64_RECOMPUTE 2u /* recompute pixels with det <= tau*a*d*f in FP64 */
+
+/* bits of the optional per-pixel status plane */
+#define ZINV_PIX_NOT_PD 1u     /* det <= 0 or not finite: Z is not positive definite */
+#define ZINV_PIX_RECOMPUTED 2u /* the pixel was recomputed in FP64 */
+
+/* The ABI version this library implements (ZINV_ABI_VERSION). */
+int zinv_abi_version(void);
+
+/* Static string naming a return code. */
+const char* zinv_status_string(int code);
+
+/*
+ * zinv_det -- Alg. 2 of the paper (§3.1): per pixel, the three real diagonal
+ * and three complex upper cofactors (Eq. adjoint_elements), det as the real
+ * part of the first-column cofactor expansion (Eq. det, Eq. detr), one
+ * reciprocal t = 1/det, and Z^-1 = t * adj(Z) (Eq. inv_adjoint).
+ *
+ *   z      [9][ld] packed input (read only), n pixels.
+ *   n      number of pixels, n >= 0 (n == 0 enqueues only the counter reset).
+ *   ld     plane stride of z and zinv in floats, ld >= n.  With ld % 4 == 0 and
+ *          16-byte aligned z, zinv, det (and 4-byte aligned status) the kernel
+ *          moves four pixels per thread with 128-bit accesses; otherwise one.
+ *   zinv   [9][ld] packed output: the upper triangle of Z^-1.  zinv == z (in
+ *          place) is allowed; any other overlap with an input is not.
+ *   det    [n] output: det Z.
+ *   flags  ZINV_PLAIN, or ZINV_COMPENSATED and/or ZINV_FP64_RECOMPUTE.
+ *   tau    threshold of ZINV_FP64_RECOMPUTE: a pixel is recomputed in FP64 when
+ *          !(det > tau*a*d*f) (Hadamard: 0 < det <= a*d*f for positive definite
+ *          Z).  Must be finite and >= 0; ignored without the flag.
+ *   status [n] optional (NULL): per-pixel ZINV_PIX_* bits.
+ *   counts [2] optional (NULL), device int64: overwritten with the number of
+ *          pixels flagged ZINV_PIX_NOT_PD and ZINV_PIX_RECOMPUTED.
+ */
+int zinv_det(const float* z, int64_t n, int64_t ld, float* zinv, float* det, uint32_t flags,
+             float tau, uint8_t* status, int64_t* counts, void* stream);
+
+/*
+ * chol_zinv_det -- the paper's baseline, Alg. 1 (§2.2): Z = L L^H with three
+ * square roots and three reciprocals, T = L^-1, det = (l00 l11 l22)^2 and
+ * Z^-1 = T^H T.  The paper's printed l21 is the conjugate of the correct one;
+ * this kernel uses l21 = (conj(e) - l20 conj(l10)) / l11, which follows from
+ * Z = L L^H.  Same layout, alignment rules and outputs as zinv_det; flags must
+ * be ZINV_PLAIN (tau is ignored); status/counts report ZINV_PIX_NOT_PD.
+ */
+int chol_zinv_det(const float* z, int64_t n, int64_t ld, float* zinv, float* det,
+                  uint32_t flags, float tau, uint8_t* status, int64_t* counts, void* stream);
+
+/*
+ * zinv_det_bwd -- backward of (Z^-1, det, log det) w.r.t. the nine packed reals
+ * of Z, from the forward's saved outputs W = Z^-1 and det.  With G the
+ * Hermitian matrix of the upstream packed gradient (G_ii = g_ii,
+ * G_ij = (g_Re + i g_Im)/2 for i < j),
+ *     M = -W G W + (g_det * det + g_logdet) * W,
+ * and the output is [M00, 2Re M01, 2Im M01, 2Re M02, 2Im M02, M11, 2Re M12,
+ * 2Im M12, M22] (dL = Re tr(M dZ); the factor 2 counts both off-diagonal
+ * entries each packed real stands for).  The paper has no backward; this
+ * differentiates Eq. inv_adjoint and Eq. det.
+ *
+ *   zinv    [9][ld] packed W (read only).
+ *   det     [n] det Z (read only).
+ *   g_zinv  [9][ld] upstream gradient of the packed W, or NULL (zero).
+ *   g_det   [n] upstream gradient of det, or NULL (zero).
+ *   g_logdet [n] upstream gradient of log det, or NULL (zero).
+ *   g_z     [9][ld] output; may alias g_zinv exactly, nothing else.
+ * 128-bit path when ld % 4 == 0 and every pointer is 16-byte aligned.
+ */
+int zinv_det_bwd(const float* zinv, const float* det, int64_t n, int64_t ld,
+                 const float* g_zinv, const float* g_det, const float* g_logdet, float* g_z,
+                 void* stream);
+
+/*
+ * zinv_det_host -- zinv_det over HOST buffers, streamed through the GPU in
+ * chunks (the paper's §4.3: data larger than device memory is fed in pieces,
+ * processed and pulled back).  Copies in, kernel and copies out of successive
+ * chunks overlap on three streams the library creates once per device.
+ *
+ *   z_host, zinv_host, det_host  host buffers in the layout above (zinv_host
+ *          [9][ld], det_host [n]); page-locked (cudaHostAlloc / pinned torch
+ *          tensors) for the copies to be asynchronous.
+ *   d_ws, ws_bytes  caller-owned device workspace, at least
+ *          zinv_det_host_workspace_bytes(chunk) bytes for some chunk >= 1;
+ *          the chunk is the largest that fits (a multiple of 4 pixels when
+ *          ws_bytes allows).
+ *   flags, tau  as zinv_det.
+ * The call is asynchronous with respect to the host and ordered after prior
+ * work on `stream`; later work on `stream` waits for the last chunk to land.
+ * The host buffers must stay valid until then.  Not re-entrant: two calls on
+ * the same device must not overlap in time.
+ */
+size_t zinv_det_host_workspace_bytes(int64_t chunk);
+int zinv_det_host(const float* z_host, int64_t n, int64_t ld, float* zinv_host,
+                  float* det_host, uint32_t flags, float tau, void* d_ws, size_t ws_bytes,
+                  void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZINV_H */

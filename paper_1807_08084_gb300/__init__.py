@@ -1,0 +1,238 @@
+"""GB300-native inverse and determinant of per-pixel 3x3 Hermitian PolSAR matrices.
+
+Thin Python binding over the C ABI of ``libzinv.so`` (declared in
+``include/zinv.h``): each function checks and marshals torch CUDA tensors and
+calls the entry point of the same name on the current torch stream.  All
+arithmetic runs in the library's CUDA kernels; there is no CPU path, and every
+function raises if the library cannot be built or loaded or if a tensor is not
+on a CUDA device.
+
+Method: Coelho, Cintra, Frery, Dimitrov, "Fast Matrix Inversion and Determinant
+Computation for Polarimetric Synthetic Aperture Radar", arXiv:1807.08084 --
+Alg. 2 (adjugate, §3.1) and its baseline Alg. 1 (Cholesky, §2.2).
+
+Packed layout: float32 [9, ...] planes a, Re b, Im b, Re c, Im c, d, Re e,
+Im e, f of Z = [[a, b, c], [conj b, d, e], [conj c, conj e, f]] (§2.1).
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import build as _build
+
+PLAIN = 0
+COMPENSATED = 1
+FP64_RECOMPUTE = 2
+PIX_NOT_PD = 1
+PIX_RECOMPUTED = 2
+DEFAULT_TAU = 2.0 ** -10
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+def load() -> ctypes.CDLL:
+    """Builds libzinv.so in-tree if it is missing or stale, loads it once."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build_lib("libzinv.so")
+        lib = ctypes.CDLL(str(path))
+        lib.zinv_abi_version.restype = ctypes.c_int
+        lib.zinv_status_string.restype = ctypes.c_char_p
+        lib.zinv_status_string.argtypes = [ctypes.c_int]
+        sig = [_P, _I64, _I64, _P, _P, ctypes.c_uint32, ctypes.c_float, _P, _P, _P]
+        for f in ("zinv_det", "chol_zinv_det"):
+            getattr(lib, f).argtypes = sig
+            getattr(lib, f).restype = ctypes.c_int
+        lib.zinv_det_bwd.argtypes = [_P, _P, _I64, _I64, _P, _P, _P, _P, _P]
+        lib.zinv_det_bwd.restype = ctypes.c_int
+        lib.zinv_det_host_workspace_bytes.argtypes = [_I64]
+        lib.zinv_det_host_workspace_bytes.restype = ctypes.c_size_t
+        lib.zinv_det_host.argtypes = [_P, _I64, _I64, _P, _P, ctypes.c_uint32, ctypes.c_float,
+                                      _P, ctypes.c_size_t, _P]
+        lib.zinv_det_host.restype = ctypes.c_int
+        _declare_extra(lib)
+        if lib.zinv_abi_version() != 1:
+            raise RuntimeError("libzinv.so ABI version mismatch")
+        _lib = lib
+        return lib
+
+
+def _declare_extra(lib):
+    """Entry points beyond the per-pixel ones, declared when present."""
+    if hasattr(lib, "multilook_zinv_det"):
+        lib.multilook_zinv_det.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
+                                           ctypes.c_uint32, ctypes.c_float, _P, _P, _P]
+        lib.multilook_zinv_det.restype = ctypes.c_int
+    if hasattr(lib, "wishart_stat_fwd"):
+        lib.wishart_workspace_bytes.argtypes = [_I64, _I64, ctypes.c_int]
+        lib.wishart_workspace_bytes.restype = ctypes.c_size_t
+        lib.wishart_stat_fwd.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
+                                         _P, ctypes.c_size_t, _P]
+        lib.wishart_stat_fwd.restype = ctypes.c_int
+        lib.wishart_stat_bwd.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
+                                         _P, ctypes.c_size_t, _P]
+        lib.wishart_stat_bwd.restype = ctypes.c_int
+
+
+def status_string(code: int) -> str:
+    return load().zinv_status_string(code).decode()
+
+
+def _check(rc: int, fn: str):
+    if rc != 0:
+        raise RuntimeError(f"{fn} failed: {status_string(rc)} ({rc})")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(dev) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _planes(z: torch.Tensor, name: str = "z", nplanes: int = 9):
+    """(n, ld) of a [9, ...] float32 CUDA tensor in the packed layout."""
+    if not z.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (there is no CPU path)")
+    if z.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32")
+    if z.dim() < 2 or z.shape[0] != nplanes:
+        raise ValueError(f"{name} must have shape [{nplanes}, ...]")
+    if z.dim() == 2 and (z.stride(1) == 1 or z.shape[1] <= 1):
+        return z.shape[1], max(z.stride(0), z.shape[1])
+    if not z.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (or a [9, n] view with unit column stride)")
+    n = z[0].numel()
+    return n, n
+
+
+def _flat(x: torch.Tensor | None, n: int, name: str):
+    if x is None:
+        return None
+    if not x.is_cuda or x.dtype != torch.float32 or x.numel() != n or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {n} elements")
+    return x
+
+
+def zinv_det(z: torch.Tensor, flags: int = PLAIN, tau: float = DEFAULT_TAU,
+             want_status: bool = False, want_counts: bool = False,
+             out: tuple | None = None):
+    """Alg. 2: (Z^-1 packed like z, det [...]) [+ status uint8] [+ counts int64[2]]."""
+    return _inv_det("zinv_det", z, flags, tau, want_status, want_counts, out)
+
+
+def chol_zinv_det(z: torch.Tensor, want_status: bool = False, want_counts: bool = False,
+                  out: tuple | None = None):
+    """Alg. 1 (Cholesky route, with the corrected l21): same outputs as zinv_det."""
+    return _inv_det("chol_zinv_det", z, PLAIN, 0.0, want_status, want_counts, out)
+
+
+def _inv_det(fn, z, flags, tau, want_status, want_counts, out):
+    lib = load()
+    n, ld = _planes(z)
+    if out is None:
+        zinv = torch.empty_strided(z.shape, z.stride(), dtype=z.dtype, device=z.device)
+        det = torch.empty(z.shape[1:], dtype=torch.float32, device=z.device)
+    else:
+        zinv, det = out
+        if zinv.shape != z.shape or zinv.stride() != z.stride() or zinv.device != z.device:
+            raise ValueError("zinv must have the shape and strides of z")
+        _flat(det, n, "det")
+    status = torch.empty(z.shape[1:], dtype=torch.uint8, device=z.device) if want_status else None
+    counts = torch.empty(2, dtype=torch.int64, device=z.device) if want_counts else None
+    with torch.cuda.device(z.device):
+        rc = getattr(lib, fn)(_ptr(z), n, ld, _ptr(zinv), _ptr(det), int(flags), float(tau),
+                              _ptr(status), _ptr(counts), _stream(z.device))
+    _check(rc, fn)
+    res = (zinv, det)
+    if want_status:
+        res += (status,)
+    if want_counts:
+        res += (counts,)
+    return res
+
+
+def zinv_det_bwd(zinv: torch.Tensor, det: torch.Tensor, g_zinv=None, g_det=None,
+                 g_logdet=None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Packed gradient w.r.t. Z from W = Z^-1, det and upstream gradients (any may be None)."""
+    lib = load()
+    n, ld = _planes(zinv, "zinv")
+    _flat(det, n, "det")
+    if g_zinv is not None:
+        if g_zinv.shape != zinv.shape or g_zinv.stride() != zinv.stride():
+            raise ValueError("g_zinv must match zinv")
+    _flat(g_det, n, "g_det")
+    _flat(g_logdet, n, "g_logdet")
+    if out is None:
+        g_z = torch.empty_strided(zinv.shape, zinv.stride(), dtype=zinv.dtype, device=zinv.device)
+    else:
+        g_z = out
+        if g_z.shape != zinv.shape or g_z.stride() != zinv.stride():
+            raise ValueError("out must have the shape and strides of zinv")
+    with torch.cuda.device(zinv.device):
+        rc = lib.zinv_det_bwd(_ptr(zinv), _ptr(det), n, ld, _ptr(g_zinv), _ptr(g_det),
+                              _ptr(g_logdet), _ptr(g_z), _stream(zinv.device))
+    _check(rc, "zinv_det_bwd")
+    return g_z
+
+
+def zinv_det_host_workspace_bytes(chunk: int) -> int:
+    return int(load().zinv_det_host_workspace_bytes(int(chunk)))
+
+
+def zinv_det_host(z_host: torch.Tensor, ws: torch.Tensor, flags: int = PLAIN,
+                  tau: float = DEFAULT_TAU, out: tuple | None = None,
+                  device: torch.device | None = None):
+    """zinv_det over pinned host tensors, streamed through the device workspace `ws`
+    (a uint8 CUDA tensor of zinv_det_host_workspace_bytes(chunk) bytes).  Asynchronous:
+    synchronize the current stream before reading the outputs."""
+    lib = load()
+    if z_host.is_cuda or z_host.dtype != torch.float32 or z_host.shape[0] != 9:
+        raise ValueError("z_host must be a float32 host tensor of shape [9, ...]")
+    if not z_host.is_contiguous():
+        raise ValueError("z_host must be contiguous")
+    n = z_host[0].numel()
+    if not ws.is_cuda or ws.dtype != torch.uint8:
+        raise ValueError("ws must be a uint8 CUDA tensor")
+    if out is None:
+        zinv = torch.empty_like(z_host, pin_memory=True)
+        det = torch.empty(z_host.shape[1:], dtype=torch.float32, pin_memory=True)
+    else:
+        zinv, det = out
+    dev = ws.device if device is None else device
+    with torch.cuda.device(dev):
+        rc = lib.zinv_det_host(_ptr(z_host), n, n, _ptr(zinv), _ptr(det), int(flags), float(tau),
+                               _ptr(ws), ws.numel(), _stream(dev))
+    _check(rc, "zinv_det_host")
+    return zinv, det
+
+
+class ZInvDet(torch.autograd.Function):
+    """(Z^-1, det) = ZInvDet.apply(z) with the hand-written backward kernel.
+
+    Gradients are real partial derivatives w.r.t. the nine packed reals of z.
+    """
+
+    @staticmethod
+    def forward(ctx, z, flags: int = PLAIN, tau: float = DEFAULT_TAU):
+        zinv, det = zinv_det(z, flags, tau)
+        ctx.save_for_backward(zinv, det)
+        return zinv, det
+
+    @staticmethod
+    def backward(ctx, g_zinv, g_det):
+        zinv, det = ctx.saved_tensors
+        g_zinv = None if g_zinv is None else g_zinv.contiguous()
+        g_det = None if g_det is None else g_det.contiguous()
+        return zinv_det_bwd(zinv, det, g_zinv, g_det, None), None, None
+

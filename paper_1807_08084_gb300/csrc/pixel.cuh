@@ -1,0 +1,234 @@
+// pixel.cuh -- per-pixel device arithmetic: the adjugate inverse+det (Alg. 2 of
+// the paper) in plain FP32, FMA-compensated FP32 and FP64; the Cholesky route
+// (Alg. 1); status bits.  Nine packed reals per pixel in the paper's letter
+// order (§2.1): x = {a, Re b, Im b, Re c, Im c, d, Re e, Im e, f}.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "zinv.h"
+
+namespace zinv {
+
+// ---------------------------------------------------------------------------
+// Alg. 2 (§3.1): cofactors (Eq. adjoint_elements), det (Eq. detr), t = 1/det,
+// Z^-1 = t adj(Z) (Eq. inv_adjoint).  T = float or double.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+template <typename T>
+__device__ __forceinline__ void adjugate_inv_det(const T x[9], T w[9], T& det) {
+  const T a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
+  const T d = x[5], er = x[6], ei = x[7], f = x[8];
+  // real diagonal cofactors: a_c = d f - |e|^2, d_c = a f - |c|^2, f_c = a d - |b|^2
+  const T ac = d * f - (er * er + ei * ei);
+  const T dc = a * f - (cr * cr + ci * ci);
+  const T fc = a * d - (br * br + bi * bi);
+  // complex upper cofactors: b_c = c conj(e) - b f, c_c = b e - c d, e_c = c conj(b) - a e
+  const T bcr = (cr * er + ci * ei) - br * f;
+  const T bci = (ci * er - cr * ei) - bi * f;
+  const T ccr = (br * er - bi * ei) - cr * d;
+  const T cci = (br * ei + bi * er) - ci * d;
+  const T ecr = (cr * br + ci * bi) - a * er;
+  const T eci = (ci * br - cr * bi) - a * ei;
+  // det = a a_c + Re(conj(b) b_c) + Re(conj(c) c_c)
+  det = a * ac + br * bcr + bi * bci + cr * ccr + ci * cci;
+  const T t = recip(det);
+  w[0] = t * ac;
+  w[1] = t * bcr;
+  w[2] = t * bci;
+  w[3] = t * ccr;
+  w[4] = t * cci;
+  w[5] = t * dc;
+  w[6] = t * ecr;
+  w[7] = t * eci;
+  w[8] = t * fc;
+}
+
+// ---------------------------------------------------------------------------
+// Compensated FP32.  Error-free transforms: TwoProduct by FMA (the rounding
+// error of a*b is fma(a, b, -p) exactly) and Knuth's TwoSum; Dot2 of Ogita,
+// Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005)
+// accumulates the products' and sums' errors separately, giving a result as
+// accurate as if computed in twice the working precision.  The __f*_rn
+// intrinsics keep nvcc from contracting or re-associating them.
+// ---------------------------------------------------------------------------
+struct ff {
+  float hi, lo;  // value = hi + lo, |lo| <= ulp(hi)/2
+};
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// x0*y0 + x1*y1 + x2*y2 by Dot2, returned unevaluated as hi + lo.
+__device__ __forceinline__ ff dot3(float x0, float y0, float x1, float y1, float x2, float y2) {
+  float p, s, h, r, q;
+  two_prod(x0, y0, p, s);
+  two_prod(x1, y1, h, r);
+  two_sum(p, h, p, q);
+  s = __fadd_rn(s, __fadd_rn(q, r));
+  two_prod(x2, y2, h, r);
+  two_sum(p, h, p, q);
+  s = __fadd_rn(s, __fadd_rn(q, r));
+  ff out;
+  two_sum(p, s, out.hi, out.lo);
+  return out;
+}
+
+__device__ __forceinline__ void adjugate_inv_det_comp(const float x[9], float w[9], float& det) {
+  const float a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
+  const float d = x[5], er = x[6], ei = x[7], f = x[8];
+  const ff ac = dot3(d, f, -er, er, -ei, ei);
+  const ff dc = dot3(a, f, -cr, cr, -ci, ci);
+  const ff fc = dot3(a, d, -br, br, -bi, bi);
+  const ff bcr = dot3(cr, er, ci, ei, -br, f);
+  const ff bci = dot3(ci, er, -cr, ei, -bi, f);
+  const ff ccr = dot3(br, er, -bi, ei, -cr, d);
+  const ff cci = dot3(br, ei, bi, er, -ci, d);
+  const ff ecr = dot3(cr, br, ci, bi, -a, er);
+  const ff eci = dot3(ci, br, -cr, bi, -a, ei);
+  // det by Dot2 over the five products with the cofactors' high parts; the
+  // products with their low parts are small and join the error accumulator.
+  float p, s, h, r, q;
+  two_prod(a, ac.hi, p, s);
+  s = __fmaf_rn(a, ac.lo, s);
+  const float xs[4] = {br, bi, cr, ci};
+  const ff ys[4] = {bcr, bci, ccr, cci};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    two_prod(xs[k], ys[k].hi, h, r);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, r));
+    s = __fmaf_rn(xs[k], ys[k].lo, s);
+  }
+  float dhi, dlo;
+  two_sum(p, s, dhi, dlo);
+  det = dhi;
+  // t ~ 1/(dhi + dlo): the correctly rounded reciprocal plus one Newton-type
+  // correction using its exact residual 1 - dhi*t and the det's low part.
+  float t = __frcp_rn(dhi);
+  const float res = __fmaf_rn(-dhi, t, 1.0f);
+  t = __fmaf_rn(t, __fmaf_rn(-dlo, t, res), t);
+  const ff cof[9] = {ac, bcr, bci, ccr, cci, dc, ecr, eci, fc};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) w[k] = __fmaf_rn(cof[k].hi, t, __fmul_rn(cof[k].lo, t));
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 1 (§2.2), Cholesky route, FP32 with correctly rounded sqrt and
+// reciprocal.  Z = L L^H, L lower triangular with real positive diagonal:
+//   l00 = sqrt(a), l10 = conj(b)/l00, l20 = conj(c)/l00,
+//   l11 = sqrt(d - |l10|^2), l21 = (conj(e) - l20 conj(l10)) / l11,
+//   l22 = sqrt(f - |l20|^2 - |l21|^2);
+// T = L^-1 (lower triangular), det = (l00 l11 l22)^2, Z^-1 = T^H T.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cholesky_inv_det(const float x[9], float w[9], float& det) {
+  const float a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
+  const float d = x[5], er = x[6], ei = x[7], f = x[8];
+  const float l00 = __fsqrt_rn(a);
+  const float v0 = __frcp_rn(l00);
+  const float l10r = br * v0, l10i = -bi * v0;
+  const float l20r = cr * v0, l20i = -ci * v0;
+  const float l11 = __fsqrt_rn(d - (l10r * l10r + l10i * l10i));
+  const float v1 = __frcp_rn(l11);
+  // conj(e) - l20 conj(l10)
+  const float nr = er - (l20r * l10r + l20i * l10i);
+  const float ni = -ei - (l20i * l10r - l20r * l10i);
+  const float l21r = nr * v1, l21i = ni * v1;
+  const float l22 = __fsqrt_rn(f - (l20r * l20r + l20i * l20i) - (l21r * l21r + l21i * l21i));
+  const float v2 = __frcp_rn(l22);
+  // T = L^-1: t00 = v0, t11 = v1, t22 = v2, t10 = -l10 v0 v1, t21 = -l21 v1 v2,
+  // t20 = v2 v0 (l21 l10 v1 - l20)
+  const float v01 = v0 * v1, v12 = v1 * v2, v02 = v0 * v2;
+  const float t10r = -l10r * v01, t10i = -l10i * v01;
+  const float t21r = -l21r * v12, t21i = -l21i * v12;
+  const float pr = (l21r * l10r - l21i * l10i) * v1 - l20r;
+  const float pi = (l21r * l10i + l21i * l10r) * v1 - l20i;
+  const float t20r = pr * v02, t20i = pi * v02;
+  const float ld = l00 * l11 * l22;
+  det = ld * ld;
+  // Z^-1 = T^H T (upper triangle)
+  w[0] = v0 * v0 + (t10r * t10r + t10i * t10i) + (t20r * t20r + t20i * t20i);
+  // conj(t10) t11 + conj(t20) t21
+  w[1] = t10r * v1 + (t20r * t21r + t20i * t21i);
+  w[2] = -t10i * v1 + (t20r * t21i - t20i * t21r);
+  // conj(t20) t22
+  w[3] = t20r * v2;
+  w[4] = -t20i * v2;
+  w[5] = v1 * v1 + (t21r * t21r + t21i * t21i);
+  // conj(t21) t22
+  w[6] = t21r * v2;
+  w[7] = -t21i * v2;
+  w[8] = v2 * v2;
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch over the algorithm variants; returns the pixel's ZINV_PIX_* bits.
+// ---------------------------------------------------------------------------
+enum Alg : int { kPlain = 0, kComp = 1, kPlainF64 = 2, kCompF64 = 3, kChol = 4 };
+
+template <int ALG>
+__device__ __forceinline__ uint32_t pixel_inv_det(const float x[9], float w[9], float& det,
+                                                  float tau) {
+  if (ALG == kChol) {
+    cholesky_inv_det(x, w, det);
+  } else if (ALG == kComp || ALG == kCompF64) {
+    adjugate_inv_det_comp(x, w, det);
+  } else {
+    adjugate_inv_det<float>(x, w, det);
+  }
+  uint32_t st = 0;
+  if (ALG == kPlainF64 || ALG == kCompF64) {
+    // Hadamard ratio det/(a d f) in (0, 1] for positive definite Z; a small
+    // ratio means cancellation ate the FP32 digits.  !(>) also catches NaN.
+    if (!(det > tau * (x[0] * x[5] * x[8]))) {
+      double xd[9], wd[9], dd;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) xd[k] = (double)x[k];
+      adjugate_inv_det<double>(xd, wd, dd);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) w[k] = __double2float_rn(wd[k]);
+      det = __double2float_rn(dd);
+      st |= ZINV_PIX_RECOMPUTED;
+      if (!(dd > 0.0) || !isfinite(dd)) st |= ZINV_PIX_NOT_PD;
+      return st;
+    }
+  }
+  if (!(det > 0.0f) || !isfinite(det)) st |= ZINV_PIX_NOT_PD;
+  return st;
+}
+
+// float4 lane access with a compile-time lane after unrolling
+__device__ __forceinline__ float lane(const float4& v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void set_lane(float4& v, int j, float x) {
+  if (j == 0) v.x = x;
+  else if (j == 1) v.y = x;
+  else if (j == 2) v.z = x;
+  else v.w = x;
+}
+
+// Warp-aggregated add of two per-thread counters into device counters.
+__device__ __forceinline__ void add_counts(unsigned long long* counts, uint32_t c0, uint32_t c1) {
+  const unsigned mask = __activemask();
+  const uint32_t s0 = __reduce_add_sync(mask, c0);
+  const uint32_t s1 = __reduce_add_sync(mask, c1);
+  const int leader = __ffs(mask) - 1;
+  if ((int)(threadIdx.x & 31) == leader) {
+    if (s0) atomicAdd(counts, (unsigned long long)s0);
+    if (s1) atomicAdd(counts + 1, (unsigned long long)s1);
+  }
+}
+
+}  // namespace zinv

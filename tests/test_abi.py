@@ -1,0 +1,76 @@
+"""The C ABI without a GPU: the library loads, exports every symbol that
+include/*.h declares, and rejects bad arguments on the host before touching a
+device.  (No compute call is made here.)"""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+DECL = re.compile(r"^\s*(?:int|size_t|const\s+char\s*\*)\s+(\w+)\s*\(", re.M)
+
+
+def declared(header: Path):
+    return DECL.findall(header.read_text())
+
+
+def test_headers_declare_entry_points():
+    names = [n for h in sorted((ROOT / "include").glob("*.h")) for n in declared(h)]
+    for must in ("zinv_det", "chol_zinv_det", "zinv_det_bwd", "zinv_abi_version",
+                 "zinv_status_string", "zinv_det_host"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1807_08084_gb300 as zp
+    lib = zp.load()
+    missing = [n for h in sorted((ROOT / "include").glob("*.h")) for n in declared(h)
+               if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+    assert lib.zinv_abi_version() == 1
+    assert zp.status_string(0) == "ok"
+    assert "argument" in zp.status_string(-1)
+
+
+def test_synth_library_loads():
+    from paper_1807_08084_gb300.synth import gpu
+    lib = gpu.load()
+    for n in ("synth_z_wishart", "synth_z_cond", "synth_z_rrh", "synth_slc", "synth_uniform"):
+        assert hasattr(lib, n)
+
+
+def _call(fn, z, n, ld, zinv, det, flags=0, tau=0.001, status=None, counts=None):
+    P = ctypes.c_void_p
+    return fn(P(z), n, ld, P(zinv), P(det), flags, tau, P(status), P(counts), None)
+
+
+def test_host_argument_checks():
+    """Argument errors come back as ZINV_ERR_ARG before any device work; valid
+    arguments on a machine without a GPU come back as ZINV_ERR_DEVICE."""
+    import torch
+    import paper_1807_08084_gb300 as zp
+    lib = zp.load()
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    fake = 0x10000  # never dereferenced: the call must fail before any access
+    for fn in (lib.zinv_det, lib.chol_zinv_det):
+        assert _call(fn, fake, -1, 0, fake, fake) == -1            # n < 0
+        assert _call(fn, fake, 10, 5, fake, fake) == -1            # ld < n
+        assert _call(fn, None, 10, 10, fake, fake) == -1           # null input
+        assert _call(fn, fake, 10, 10, None, fake) == -1           # null output
+        assert _call(fn, fake + 2, 10, 10, fake, fake) == -1       # misaligned
+        assert _call(fn, fake, 10, 10, fake, fake, tau=float("nan")) == -1
+        assert _call(fn, fake, 10, 10, fake, fake, tau=-1.0) == -1
+        assert _call(fn, fake, 10, 10, fake, fake, counts=fake + 4) == -1
+        assert _call(fn, fake, 10, 10, fake, fake) == -3           # valid, no device
+    assert _call(lib.zinv_det, fake, 10, 10, fake, fake, flags=4) == -1  # unknown flag
+    assert _call(lib.chol_zinv_det, fake, 10, 10, fake, fake, flags=1) == -1
+    P = ctypes.c_void_p
+    assert lib.zinv_det_bwd(P(fake), P(fake), 10, 5, None, None, None, P(fake), None) == -1
+    assert lib.zinv_det_bwd(P(fake), None, 10, 10, None, P(fake), None, P(fake), None) == -1
+    assert lib.zinv_det_bwd(P(fake), P(fake), 10, 10, P(fake), None, None, P(fake), None) == -3
+    assert lib.zinv_det_host(P(fake), 10, 10, P(fake), P(fake), 0, 0.0, P(fake + 16), 1 << 20,
+                             None) == -1  # workspace not 256-byte aligned
+    assert lib.zinv_det_host_workspace_bytes(0) == 0
+    assert lib.zinv_det_host_workspace_bytes(1024) >= 3 * 40 * 1024

@@ -1,0 +1,301 @@
+"""GPU parity of the per-pixel kernels (zinv_det in every mode, chol_zinv_det,
+zinv_det_bwd, zinv_det_host) against the FP64 oracle, through the C ABI.
+
+Tolerance (stated for FP32 inverse and det): per pixel, max relative entrywise
+error <= 1e-5 * cond_2(Z), where the diagonal error is |dW_ii|/W_ii, the
+off-diagonal error |dW_ij|/sqrt(W_ii W_jj) (a bound on |W_ij| for positive
+definite W), and cond_2 comes from the oracle on the FP32 input.  Repeated GPU
+runs must agree bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+from helpers import det_err, inv_err, unpack
+
+from paper_1807_08084_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+MODES = {
+    "plain": ("zinv_det", 0),
+    "compensated": ("zinv_det", 1),
+    "plain_fp64": ("zinv_det", 2),
+    "compensated_fp64": ("zinv_det", 3),
+    "cholesky": ("chol_zinv_det", 0),
+}
+
+
+def strided(a, ld: int) -> torch.Tensor:
+    """[9, n] CUDA view with plane stride ld (>= n) holding a copy of a."""
+    a = torch.as_tensor(a).cuda()
+    n = a.shape[1]
+    t = torch.as_strided(torch.zeros(9 * ld, device="cuda"), (9, n), (ld, 1))
+    t.copy_(a)
+    return t
+
+
+def odd_ld(n: int) -> int:
+    return n + 1 if (n + 1) % 4 else n + 2
+
+
+def run_mode(zp, z, mode, **kw):
+    fn, flags = MODES[mode]
+    if fn == "chol_zinv_det":
+        return zp.chol_zinv_det(z, **kw)
+    return zp.zinv_det(z, flags, **kw)
+
+
+def check_parity(orc, z_np, zinv_gpu, det_gpu, tol=TOL, mask=None):
+    ref_inv, ref_det = orc.zinv_det(z_np)
+    cond = orc.cond(z_np)
+    pd = np.isfinite(cond) & (ref_det > 0)
+    if mask is not None:
+        pd &= mask
+    ei = inv_err(zinv_gpu, ref_inv)
+    ed = det_err(det_gpu, ref_det)
+    bad = pd & ~((ei <= tol * cond) & (ed <= tol * cond))
+    assert not bad.any(), (
+        f"{bad.sum()} of {pd.sum()} pixels out of tolerance; worst inv err/cond "
+        f"{np.nanmax(ei[pd] / cond[pd]):.3e}, det err/cond {np.nanmax(ed[pd] / cond[pd]):.3e}")
+    return ei[pd], ed[pd], cond[pd]
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_plain_workload_full(zlib, orc, mode):
+    """256 x 256, N = 4 looks of the fixed Sigma: every pixel against the oracle."""
+    w = S.WORKLOADS["plain_256"]
+    z_np = w.packed_z()
+    z = torch.from_numpy(z_np).cuda().reshape(9, w.H, w.W)
+    zinv, det, status, counts = run_mode(zlib, z, mode, want_status=True, want_counts=True)
+    torch.cuda.synchronize()
+    check_parity(orc, z_np, zinv.cpu().numpy().reshape(9, -1), det.cpu().numpy().ravel())
+    assert int(counts[0]) == 0 and int((status & 1).sum()) == 0
+    # bit-exact repeat
+    zinv2, det2 = run_mode(zlib, z, mode)
+    assert torch.equal(zinv, zinv2) and torch.equal(det, det2)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 255, 1023, 4097, 65537])
+@pytest.mark.parametrize("mode", ["plain", "compensated", "cholesky"])
+def test_ragged_sizes_and_both_paths(zlib, orc, n, mode):
+    """Tails that do not fill a float4, the 128-bit path (ld % 4 == 0) and the
+    one-pixel path (ld % 4 != 0) give the same bits and match the oracle."""
+    w = S.WORKLOADS["paper_sim"]
+    z_np = w.packed_z(np.arange(n, dtype=np.uint64))
+    z_vec = strided(z_np, (n + 3) // 4 * 4)
+    z_sca = strided(z_np, odd_ld(n))
+    a_inv, a_det = run_mode(zlib, z_vec, mode)
+    b_inv, b_det = run_mode(zlib, z_sca, mode)
+    torch.cuda.synchronize()
+    assert torch.equal(a_inv.contiguous(), b_inv.contiguous()) and torch.equal(a_det, b_det)
+    check_parity(orc, z_np, a_inv.cpu().numpy(), a_det.cpu().numpy())
+
+
+def test_empty_input(zlib):
+    z = torch.empty((9, 0), device="cuda")
+    zinv, det, counts = zlib.zinv_det(z, want_counts=True)
+    torch.cuda.synchronize()
+    assert zinv.shape == (9, 0) and det.shape == (0,) and counts.tolist() == [0, 0]
+
+
+def test_in_place(zlib, orc):
+    w = S.WORKLOADS["plain_256"]
+    z_np = w.packed_z(np.arange(10001, dtype=np.uint64))
+    z = torch.from_numpy(z_np).cuda()
+    ref_inv, ref_det = zlib.zinv_det(z.clone())
+    det = torch.empty(z.shape[1], device="cuda")
+    zlib.zinv_det(z, out=(z, det))
+    torch.cuda.synchronize()
+    assert torch.equal(z, ref_inv) and torch.equal(det, ref_det)
+
+
+def test_not_pd_and_non_finite_pixels(zlib):
+    """Bad pixels are flagged in the status plane and counted; nothing traps."""
+    rows = [
+        [1, 0, 0, 0, 0, 1, 0, 0, 1],          # identity (good)
+        [0, 0, 0, 0, 0, 0, 0, 0, 0],          # zero matrix
+        [1, 2, 0, 0, 0, 1, 0, 0, 1],          # indefinite (det < 0)
+        [-1, 0, 0, 0, 0, -1, 0, 0, 1],        # det > 0 but not PD (two negative eigenvalues)
+        [float("nan")] + [0] * 8,             # NaN
+        [float("inf"), 0, 0, 0, 0, 1, 0, 0, 1],
+        [1, 1, 0, 0, 0, 1, 0, 0, 1],          # singular (det = 0)
+    ]
+    z_np = np.array(rows, dtype=np.float32).T.copy()
+    z = torch.from_numpy(z_np).cuda()
+    for mode in MODES:
+        zinv, det, st, cnt = run_mode(zlib, z, mode, want_status=True, want_counts=True)
+        torch.cuda.synchronize()
+        st = st.cpu().numpy()
+        not_pd = (st & 1).astype(bool)
+        assert not not_pd[0]
+        assert not_pd[[1, 2, 4, 5, 6]].all(), (mode, st)
+        assert int(cnt[0]) == int(not_pd.sum())
+        if mode.endswith("fp64"):
+            assert int(cnt[1]) == int(((st & 2) > 0).sum()) >= 5
+        # a det > 0 matrix with two negative eigenvalues passes the det test of the
+        # adjugate route (Eq. det cannot see it); the Cholesky route fails on it
+        if mode == "cholesky":
+            assert not_pd[3]
+
+
+def test_fp64_flag_and_counts(zlib, orc):
+    """Pixels with det <= tau * a d f are recomputed in FP64 and counted; the
+    recomputed ones match the oracle to FP32 rounding."""
+    w = S.WORKLOADS["precision_4k"]
+    idx = np.arange(200000, dtype=np.uint64)
+    z_np = w.packed_z(idx)
+    z = torch.from_numpy(z_np).cuda()
+    tau = 2.0 ** -10
+    zinv, det, st, cnt = zlib.zinv_det(z, 2, tau, want_status=True, want_counts=True)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    rec = (st & 2) > 0
+    zz = z_np.astype(np.float64)
+    ref_inv, ref_det = orc.zinv_det(z_np)
+    # the flag decision, re-taken in FP32 exactly as the kernel does, on the kernel's det
+    plain_inv, plain_det = zlib.zinv_det(z, 0)
+    pdet = plain_det.cpu().numpy()
+    adf = (z_np[0] * z_np[5]).astype(np.float32) * z_np[8]
+    expect = ~(pdet > np.float32(tau) * adf)
+    assert np.array_equal(rec, expect)
+    assert int(cnt[1]) == int(rec.sum()) > 0
+    # NOT_PD in FP64 mode is the FP64 sign of det, as the oracle's
+    not_pd = (st & 1) > 0
+    assert np.array_equal(not_pd, ~(ref_det > 0))
+    # recomputed pixels: FP64 then one FP32 rounding
+    good = rec & (ref_det > 0)
+    ei = inv_err(zinv.cpu().numpy()[:, good], ref_inv[:, good])
+    ed = det_err(det.cpu().numpy()[good], ref_det[good])
+    assert ei.max() < 1e-6 and ed.max() < 1e-6
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_precision_workload_tolerance(zlib, orc, mode):
+    """cond log-uniform in [1, 1e7]: every positive-definite pixel within 1e-5 cond."""
+    w = S.WORKLOADS["precision_4k"]
+    z_np = w.packed_z(np.arange(100000, dtype=np.uint64))
+    z = torch.from_numpy(z_np).cuda()
+    zinv, det = run_mode(zlib, z, mode)
+    torch.cuda.synchronize()
+    ei, ed, cond = check_parity(orc, z_np, zinv.cpu().numpy(), det.cpu().numpy())
+    if mode.startswith("compensated"):
+        # compensation removes the cond-proportional term for moderate cond
+        m = cond < 1e4
+        assert np.max(ei[m]) < 1e-5 and np.max(ed[m]) < 1e-5
+
+
+def test_generator_twin_bit_exact(zlib):
+    """The GPU generator reproduces the numpy twin bit for bit at sampled pixels."""
+    from paper_1807_08084_gb300.synth import gpu as G
+    rng = np.random.default_rng(5)
+    for name in ("plain_256", "precision_4k", "paper_sim", "paper_meas_shaped"):
+        w = S.WORKLOADS[name]
+        if w.n > 5_000_000:
+            w = S.scaled(w, 1, 2_000_000)
+        zg = G.packed_z(w).reshape(9, -1)
+        idx = np.unique(rng.integers(0, w.n, 3000)).astype(np.uint64)
+        got = zg[:, torch.from_numpy(idx.astype(np.int64)).cuda()].cpu().numpy()
+        np.testing.assert_array_equal(got, w.packed_z(idx), err_msg=name)
+    for name in ("multilook_8k", "wishart_pair_4k"):
+        w = S.scaled(S.WORKLOADS[name], 512, 384)
+        for date in (0, 1):
+            sg = G.image(w, date).reshape(3, -1)
+            idx = np.unique(rng.integers(0, w.n, 3000)).astype(np.uint64)
+            got = sg[:, torch.from_numpy(idx.astype(np.int64)).cuda()].cpu().numpy()
+            np.testing.assert_array_equal(got, w.looks(idx, date), err_msg=f"{name} {date}")
+    u = G.uniform(7, 1000).cpu().numpy()
+    np.testing.assert_array_equal(u, S.uniform_f32(7, np.arange(1000, dtype=np.uint64)))
+
+
+def test_scale_workload_full_size_sampled(zlib, orc):
+    """16384 x 16384 (268M pixels) generated on the GPU, inverted in the launch
+    configuration the benchmark times; 200k sampled pixels against the oracle on
+    inputs regenerated by the numpy twin."""
+    from paper_1807_08084_gb300.synth import gpu as G
+    w = S.WORKLOADS["scale_16k"]
+    z = G.packed_z(w)
+    rng = np.random.default_rng(6)
+    idx = np.unique(rng.integers(0, w.n, 200000))
+    it = torch.from_numpy(idx).cuda()
+    z_np = w.packed_z(idx.astype(np.uint64))
+    np.testing.assert_array_equal(z.reshape(9, -1)[:, it].cpu().numpy(), z_np)
+    for mode in ("plain", "compensated", "plain_fp64", "cholesky"):
+        zinv, det = run_mode(zlib, z, mode)
+        torch.cuda.synchronize()
+        check_parity(orc, z_np, zinv.reshape(9, -1)[:, it].cpu().numpy(),
+                     det.reshape(-1)[it].cpu().numpy())
+        del zinv, det
+    # the last pixel (a ragged-free size, but the final group of the grid-stride loop)
+    last = np.array([w.n - 1], dtype=np.uint64)
+    zinv, det = zlib.zinv_det(z)
+    ref_inv, ref_det = orc.zinv_det(w.packed_z(last))
+    assert det_err(det.reshape(-1)[-1:].cpu().numpy(), ref_det)[0] < 1e-3
+
+
+def _bwd_tol_check(orc, z_np, gz_gpu, gW, gd, gl, tol=TOL):
+    ref = orc.zinv_det_bwd(z_np, gW, gd, gl)
+    W, det = orc.zinv_det(z_np)
+    cond = orc.cond(z_np)
+    Wn = np.abs(unpack(W)).max(axis=(1, 2))
+    s = np.zeros(z_np.shape[1])
+    if gd is not None:
+        s += np.abs(gd) * np.abs(det)
+    if gl is not None:
+        s += np.abs(gl)
+    scale = Wn * Wn * (0 if gW is None else np.abs(gW).max(axis=0)) + s * Wn
+    err = np.abs(gz_gpu - ref).max(axis=0) / scale
+    assert np.all(err <= tol * cond), f"worst bwd err/cond {np.max(err / cond):.3e}"
+
+
+@pytest.mark.parametrize("which", ["W", "det", "logdet", "all"])
+def test_bwd_parity(zlib, orc, which):
+    w = S.WORKLOADS["plain_256"]
+    n = 50001
+    idx = np.arange(n, dtype=np.uint64)
+    z_np = w.packed_z(idx)
+    z = torch.from_numpy(z_np).cuda()
+    zinv, det = zlib.zinv_det(z)
+    gW = np.stack([S.uniform_f32(11, idx, stream=k) for k in range(9)])
+    gd = S.uniform_f32(12, idx)
+    gl = S.uniform_f32(13, idx)
+    use = {"W": (gW, None, None), "det": (None, gd, None), "logdet": (None, None, gl),
+           "all": (gW, gd, gl)}[which]
+    args = [None if a is None else torch.from_numpy(a).cuda() for a in use]
+    gz = zlib.zinv_det_bwd(zinv, det, *args)
+    torch.cuda.synchronize()
+    _bwd_tol_check(orc, z_np, gz.cpu().numpy(), *use)
+    # one-pixel path (ld % 4 != 0) gives the same bits
+    ld = odd_ld(n)
+    a2 = [None if a is None else (a.clone() if a.dim() == 1 else strided(a, ld)) for a in args]
+    gz2 = zlib.zinv_det_bwd(strided(zinv, ld), det, *a2)
+    torch.cuda.synchronize()
+    assert torch.equal(gz2.contiguous(), gz)
+
+
+def test_autograd_function(zlib):
+    import paper_1807_08084_gb300 as zp
+    w = S.WORKLOADS["plain_256"]
+    z = torch.from_numpy(w.packed_z(np.arange(4096, dtype=np.uint64))).cuda().requires_grad_()
+    gW = torch.randn(9, 4096, device="cuda")
+    gd = torch.randn(4096, device="cuda")
+    zinv, det = zp.ZInvDet.apply(z)
+    (zinv * gW).sum().add_((det * gd).sum()).backward()
+    direct = zp.zinv_det_bwd(zinv.detach(), det.detach(), gW, gd, None)
+    torch.cuda.synchronize()
+    assert torch.equal(z.grad, direct)
+
+
+def test_host_streaming_matches_device(zlib):
+    w = S.WORKLOADS["paper_sim"]
+    n = 1_000_003
+    z = torch.from_numpy(w.packed_z(np.arange(n, dtype=np.uint64)))
+    z_pin = z.pin_memory()
+    ref_inv, ref_det = zlib.zinv_det(z.cuda())
+    for chunk in (4096, 100_000, n + 10):
+        ws = torch.empty(zlib.zinv_det_host_workspace_bytes(chunk), dtype=torch.uint8,
+                         device="cuda")
+        zinv_h, det_h = zlib.zinv_det_host(z_pin, ws)
+        torch.cuda.synchronize()
+        assert torch.equal(zinv_h, ref_inv.cpu()) and torch.equal(det_h, ref_det.cpu())
