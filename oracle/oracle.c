@@ -12,10 +12,13 @@
  * Radar", arXiv:1807.08084.
  *
  * What each exported function computes, and what pins it (the tests):
- *   oracle_zinv_det        det by first-column cofactor expansion (Eq. det, §3.1),
- *                          inverse by Gauss-Jordan elimination with partial
+ *   oracle_zinv_det        inverse by Gauss-Jordan elimination with partial
  *                          pivoting (the plain definition A X = I; independent of
- *                          the adjugate route of Eq. inv_adjoint).  Pinned by exact
+ *                          the adjugate route of Eq. inv_adjoint), det as the
+ *                          product of its pivots (the determinant Eq. det
+ *                          expands, evaluated backward-stably: a cofactor
+ *                          expansion in FP64 loses u64 cond lmax/lmid, 1e-2 at
+ *                          cond 1e7, while elimination keeps u64 cond).  Pinned by exact
  *                          rational arithmetic on a fixed matrix, numpy.linalg on
  *                          random matrices, Z Z^-1 = I, diagonal and block-diagonal
  *                          closed forms (§5), U diag(l) U^H with known l.
@@ -172,13 +175,19 @@ static cplx det_by_row(const mat3* A, int i)
 
 /* ------------------------------------------------------------------------ */
 /* Inverse by Gauss-Jordan elimination with partial pivoting on [A | I].     */
-/* This is the plain definition (solve A X = I) and uses no cofactor.       */
-/* Returns 0 on success, -1 if a pivot is exactly zero (singular).          */
+/* This is the plain definition (solve A X = I) and uses no cofactor.  The  */
+/* same elimination gives det A as the product of the pivots times the sign */
+/* of the row permutation.  Both are backward stable: their error is of     */
+/* order u * cond(A), whereas a cofactor expansion evaluated in floating    */
+/* point loses u * cond(A) * lmax/lmid when two eigenvalues are small.      */
+/* Returns 0 on success, -1 if a pivot is exactly zero (singular, det 0).   */
 /* ------------------------------------------------------------------------ */
 
-static int ge_inverse(const mat3* A, mat3* X)
+static int ge_inverse_det(const mat3* A, mat3* X, cplx* det)
 {
     cplx M[3][6];
+    cplx prod = 1.0;
+    int swaps = 0;
     for (int i = 0; i < 3; ++i) {
         for (int j = 0; j < 3; ++j) {
             M[i][j] = A->m[i][j];
@@ -189,14 +198,19 @@ static int ge_inverse(const mat3* A, mat3* X)
         int piv = col;
         for (int r = col + 1; r < 3; ++r)
             if (cabs(M[r][col]) > cabs(M[piv][col])) piv = r;
-        if (cabs(M[piv][col]) == 0.0) return -1;
+        if (cabs(M[piv][col]) == 0.0) {
+            if (det) *det = 0.0;
+            return -1;
+        }
         if (piv != col) {
+            ++swaps;
             for (int k = 0; k < 6; ++k) {
                 cplx t = M[col][k];
                 M[col][k] = M[piv][k];
                 M[piv][k] = t;
             }
         }
+        prod *= M[col][col];
         cplx inv_p = 1.0 / M[col][col];
         for (int k = 0; k < 6; ++k) M[col][k] *= inv_p;
         for (int r = 0; r < 3; ++r) {
@@ -207,7 +221,23 @@ static int ge_inverse(const mat3* A, mat3* X)
     }
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) X->m[i][j] = M[i][3 + j];
+#if ORACLE_MUTANT == 11
+    if (det) *det = prod; /* mutant: permutation sign ignored */
+#else
+    if (det) *det = (swaps % 2) ? -prod : prod;
+#endif
     return 0;
+}
+
+static int ge_inverse(const mat3* A, mat3* X) { return ge_inverse_det(A, X, NULL); }
+
+/* det A by elimination (see ge_inverse_det); 0 for an exactly singular A. */
+static cplx det_ge(const mat3* A)
+{
+    mat3 X;
+    cplx d = 0.0;
+    ge_inverse_det(A, &X, &d);
+    return d;
 }
 
 /* Inverse through the adjoint (Eq. inv_adjoint): X[i][j] = C[j][i] / det A. */
@@ -314,23 +344,23 @@ int oracle_version(void) { return ORACLE_VERSION; }
 /*
  * z:    [9][ld] packed Hermitian input (§2.1), n pixels.
  * zinv: [9][n] packed upper triangle of Z^-1 by Gauss-Jordan elimination.
- * det:  [n] real part of the first-column cofactor expansion (Eq. det).
- * det_im (may be NULL): [n] its imaginary part, zero for Hermitian input (§3.1).
- * A singular pixel (zero pivot) gets NaN in zinv.
+ * det:  [n] det Z (real for Hermitian Z, §3.1) from the same elimination: the
+ *       value of the cofactor expansion of Eq. det, evaluated backward-stably.
+ * det_im (may be NULL): [n] its imaginary part, zero up to rounding.
+ * A singular pixel (zero pivot) gets NaN in zinv and det 0.
  */
 void oracle_zinv_det(const double* z, int64_t n, int64_t ld, double* zinv, double* det,
                      double* det_im)
 {
     for (int64_t p = 0; p < n; ++p) {
-        mat3 A = unpack(z, ld, p);
-        cplx dt = det_by_column(&A, 0);
-        det[p] = creal(dt);
-        if (det_im) det_im[p] = cimag(dt);
-        mat3 X;
-        if (ge_inverse(&A, &X) == 0)
+        mat3 A = unpack(z, ld, p), X;
+        cplx dt = 0.0;
+        if (ge_inverse_det(&A, &X, &dt) == 0)
             pack_upper(&X, zinv, n, p);
         else
             fill_nan(zinv, n, p, 9);
+        det[p] = creal(dt);
+        if (det_im) det_im[p] = cimag(dt);
     }
 }
 
@@ -518,7 +548,7 @@ void oracle_zinv_det_bwd(const double* z, int64_t n, int64_t ld, const double* g
             fill_nan(g_z, n, p, 9);
             continue;
         }
-        double det = creal(det_by_column(&A, 0));
+        double det = creal(det_ge(&A));
         double s = 0.0;
         if (g_det) s += g_det[p] * det;
         if (g_logdet) s += g_logdet[p];
@@ -548,9 +578,9 @@ void oracle_zinv_det_bwd(const double* z, int64_t n, int64_t ld, const double* g
 /* and the loss L = sum_p q(p).  q <= 0 with equality iff Z1 = Z2.           */
 /* ------------------------------------------------------------------------ */
 
-static double logdet_cofactor(const mat3* A)
+static double logdet(const mat3* A)
 {
-    return log(creal(det_by_column(A, 0)));
+    return log(creal(det_ge(A)));
 }
 
 static double wishart_q(const mat3* Z1, const mat3* Z2)
@@ -563,7 +593,7 @@ static double wishart_q(const mat3* Z1, const mat3* Z2)
 #else
             Zm.m[i][j] = 0.5 * (Z1->m[i][j] + Z2->m[i][j]);
 #endif
-    return logdet_cofactor(Z1) + logdet_cofactor(Z2) - 2.0 * logdet_cofactor(&Zm);
+    return logdet(Z1) + logdet(Z2) - 2.0 * logdet(&Zm);
 }
 
 /* q_map: [H*W] or NULL; loss: scalar sum of q over all pixels. */

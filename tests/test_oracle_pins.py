@@ -165,6 +165,33 @@ def check_closed_forms(o):
     np.testing.assert_allclose(zinv, pack(Winv), rtol=0, atol=1e-10 * np.abs(pack(Winv)).max())
 
 
+def check_ill_conditioned_det(o):
+    """Z = U diag(1, l, l) U^H with l down to 1e-7: the oracle's det and inverse
+    against exact rational arithmetic on the very FP64 matrix it receives (two
+    small eigenvalues are where a floating-point cofactor expansion breaks down)."""
+    sympy = pytest.importorskip("sympy")
+    rng = np.random.default_rng(18)
+    n = 12
+    G = rng.standard_normal((n, 3, 3)) + 1j * rng.standard_normal((n, 3, 3))
+    U, _ = np.linalg.qr(G)
+    lam = np.stack([np.ones(n), np.logspace(-1, -7, n), np.logspace(-1, -7, n) * 0.5], axis=1)
+    z = pack((U * lam[:, None, :]) @ np.conj(np.transpose(U, (0, 2, 1))))
+    zinv, det = o.zinv_det(z)
+    A = unpack(z)
+    for p in range(n):
+        M = sympy.Matrix(3, 3, lambda i, j: sympy.Rational(float(A[p, i, j].real))
+                         + sympy.I * sympy.Rational(float(A[p, i, j].imag)))
+        d_exact = complex(sympy.N(M.det(), 30))
+        assert abs(d_exact.imag) < 1e-30
+        assert abs(det[p] - d_exact.real) <= 1e-7 * abs(d_exact.real), p
+        Minv = M.inv()
+        wa = float(sympy.re(sympy.N(Minv[0, 0], 30)))
+        wb = complex(sympy.N(Minv[0, 1], 30))
+        assert abs(zinv[0, p] - wa) <= 1e-6 * abs(wa), p
+        assert abs(zinv[1, p] + 1j * zinv[2, p] - wb) <= 1e-6 * np.sqrt(abs(wa) * abs(
+            float(sympy.re(sympy.N(Minv[1, 1], 30))))), p
+
+
 def _brute_window(s, win, w):
     """Window covariance by explicit loops (clamp-to-edge addressing)."""
     _, H, W = s.shape
@@ -279,7 +306,8 @@ def check_wishart(o):
 
 
 CHECKS = [check_sigma_exact, check_random_vs_numpy, check_identity_and_hermitian,
-          check_det_properties, check_closed_forms, check_multilook_brute,
+          check_det_properties, check_closed_forms, check_ill_conditioned_det,
+          check_multilook_brute,
           check_bwd_finite_differences, check_wishart]
 
 
@@ -300,6 +328,7 @@ MUTANTS = {
     8: "Wishart gradient drops the factor 2 on W_12",
     9: "Jacobi rotation loses the sign of tau",
     10: "gradient sign of the W G W term",
+    11: "elimination det ignores the permutation sign",
 }
 
 
