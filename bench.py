@@ -51,21 +51,22 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+def source_hash(files) -> str:
     h = hashlib.sha256()
-    for f in sorted((ROOT / "paper_1807_08084_gb300" / "csrc").glob("*")):
-        if f.suffix in (".cu", ".cuh"):
-            h.update(f.read_bytes())
+    for f in files:
+        h.update((ROOT / "paper_1807_08084_gb300" / "csrc" / f).read_bytes())
     return h.hexdigest()[:16]
 
 
 def traffic_record(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on this source."""
+    """DRAM bytes per full-size launch from the committed ncu summary
+    (profiles/traffic.json), or None once the kernel's sources have changed
+    since the counters were taken."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
     d = json.loads(p.read_text()).get(kernel)
-    if not d or d.get("source_hash") != kernel_source_hash():
+    if not d or d.get("source_hash") != source_hash(d["sources"]):
         return None
     return float(d["bytes_per_launch"])
 
@@ -199,8 +200,8 @@ def cpu_oracle_baseline(z_dev: torch.Tensor, budget_s: float = 12.0):
         done += zc.shape[1]
         p0 += chunk
     return {"value": done / spent / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {done} matrices of the same image, FP64 cofactor det + "
-                      f"Gauss-Jordan inverse, single thread ({spent:.1f} s)"}
+            "sample": f"first {done} matrices of the same image, FP64 Gauss-Jordan "
+                      f"inverse and det, single thread ({spent:.1f} s)"}
 
 
 def run_reference(args, world, rank):
@@ -241,6 +242,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sub-steps", type=int, default=50, help="steps per secondary path")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--rows", type=int, default=16384,
+                    help="image height (16384 = the full workload; smaller for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -258,6 +261,8 @@ def main():
 
     zp.load()
     w = S.WORKLOADS["scale_16k"]
+    if args.rows != w.H:
+        w = S.scaled(w, args.rows, w.W)
     if world > 1:
         from dataclasses import replace
         w = replace(w, seed=w.seed + 1000 * rank)
@@ -305,6 +310,11 @@ def main():
     paths["backward"] = {"gmat_s": n / (ms_bwd * 1e-3) / 1e9, "ms": ms_bwd, "gbs": gbs_bwd,
                          "frac_hbm": gbs_bwd / hbm_peak}
     paths["fwd_plus_bwd"] = {"gmat_s": n / ((ms + ms_bwd) * 1e-3) / 1e9, "ms": ms + ms_bwd}
+    scale = n / float(1 << 28)
+    for key, kern in (("adjugate", "zinv_det_plain_vec4"), ("cholesky", "chol_zinv_det_vec4"),
+                      ("backward", "zinv_det_bwd_vec4")):
+        t = traffic_record(kern)
+        paths[key]["dram_bytes_ncu"] = None if t is None else t * scale
     del g_w, g_det, g_z
     sampler.stop()
 
@@ -328,6 +338,8 @@ def main():
 
     cpu = cpu_oracle_baseline(z) if (rank == 0 and world == 1) else None
     traffic = traffic_record("zinv_det_plain_vec4")
+    if traffic is not None:
+        traffic *= n / float(1 << 28)
     achieved = BYTES_FWD * n / (ms * 1e-3) / 1e9
     if rank == 0:
         line = {
@@ -335,11 +347,12 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "scale_16k: 16384x16384 packed FP32 Hermitian Z "
-                                   "(268,435,456 matrices), N=16 looks, 8 class covariances "
+            "config": {"workload": f"scale_16k: {w.H}x{w.W} packed FP32 Hermitian Z "
+                                   f"({n:,} matrices), N=16 looks, 8 class covariances "
                                    "in 512x512 blocks",
                        "matrices_per_gpu": n, "bytes_per_step_per_gpu": BYTES_FWD * n,
-                       "l2": "inputs larger than L2 (20.4 GB streamed per step)",
+                       "l2": f"inputs larger than L2 ({BYTES_FWD * n / 1e9:.1f} GB streamed "
+                             "per step)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak,

@@ -48,80 +48,99 @@ __device__ __forceinline__ void adjugate_inv_det(const T x[9], T w[9], T& det) {
 }
 
 // ---------------------------------------------------------------------------
-// Compensated FP32.  Error-free transforms: TwoProduct by FMA (the rounding
-// error of a*b is fma(a, b, -p) exactly) and Knuth's TwoSum; Dot2 of Ogita,
-// Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005)
-// accumulates the products' and sums' errors separately, giving a result as
-// accurate as if computed in twice the working precision.  The __f*_rn
+// Compensated arithmetic (T = float for the compensated mode, T = double for
+// the flagged-pixel recompute).  Error-free transforms: TwoProduct by FMA (the
+// rounding error of a*b is fma(a, b, -p) exactly) and Knuth's TwoSum; Dot2 of
+// Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput.
+// 2005) accumulates the products' and sums' errors separately, so the result is
+// as accurate as if computed in twice the working precision.  The *_rn
 // intrinsics keep nvcc from contracting or re-associating them.
 // ---------------------------------------------------------------------------
-struct ff {
-  float hi, lo;  // value = hi + lo, |lo| <= ulp(hi)/2
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rcp_rn(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rcp_rn(double a) { return __drcp_rn(a); }
+
+template <typename T>
+struct dd {
+  T hi, lo;  // value = hi + lo, |lo| <= ulp(hi)/2
 };
 
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = __fmul_rn(a, b);
-  e = __fmaf_rn(a, b, -p);
+template <typename T>
+__device__ __forceinline__ void two_prod(T a, T b, T& p, T& e) {
+  p = mul_rn(a, b);
+  e = fma_rn(a, b, -p);
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float z = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+  s = add_rn(a, b);
+  const T z = sub_rn(s, a);
+  e = add_rn(sub_rn(a, sub_rn(s, z)), sub_rn(b, z));
 }
 
 // x0*y0 + x1*y1 + x2*y2 by Dot2, returned unevaluated as hi + lo.
-__device__ __forceinline__ ff dot3(float x0, float y0, float x1, float y1, float x2, float y2) {
-  float p, s, h, r, q;
+template <typename T>
+__device__ __forceinline__ dd<T> dot3(T x0, T y0, T x1, T y1, T x2, T y2) {
+  T p, s, h, r, q;
   two_prod(x0, y0, p, s);
   two_prod(x1, y1, h, r);
   two_sum(p, h, p, q);
-  s = __fadd_rn(s, __fadd_rn(q, r));
+  s = add_rn(s, add_rn(q, r));
   two_prod(x2, y2, h, r);
   two_sum(p, h, p, q);
-  s = __fadd_rn(s, __fadd_rn(q, r));
-  ff out;
+  s = add_rn(s, add_rn(q, r));
+  dd<T> out;
   two_sum(p, s, out.hi, out.lo);
   return out;
 }
 
-__device__ __forceinline__ void adjugate_inv_det_comp(const float x[9], float w[9], float& det) {
-  const float a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
-  const float d = x[5], er = x[6], ei = x[7], f = x[8];
-  const ff ac = dot3(d, f, -er, er, -ei, ei);
-  const ff dc = dot3(a, f, -cr, cr, -ci, ci);
-  const ff fc = dot3(a, d, -br, br, -bi, bi);
-  const ff bcr = dot3(cr, er, ci, ei, -br, f);
-  const ff bci = dot3(ci, er, -cr, ei, -bi, f);
-  const ff ccr = dot3(br, er, -bi, ei, -cr, d);
-  const ff cci = dot3(br, ei, bi, er, -ci, d);
-  const ff ecr = dot3(cr, br, ci, bi, -a, er);
-  const ff eci = dot3(ci, br, -cr, bi, -a, ei);
+// Alg. 2 with every cofactor and the det by Dot2 (the 2x2 products of Eq.
+// adjoint_elements are formed exactly, so cancellation in them costs nothing).
+template <typename T>
+__device__ __forceinline__ void adjugate_inv_det_comp(const T x[9], T w[9], T& det) {
+  const T a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
+  const T d = x[5], er = x[6], ei = x[7], f = x[8];
+  const dd<T> ac = dot3(d, f, -er, er, -ei, ei);
+  const dd<T> dc = dot3(a, f, -cr, cr, -ci, ci);
+  const dd<T> fc = dot3(a, d, -br, br, -bi, bi);
+  const dd<T> bcr = dot3(cr, er, ci, ei, -br, f);
+  const dd<T> bci = dot3(ci, er, -cr, ei, -bi, f);
+  const dd<T> ccr = dot3(br, er, -bi, ei, -cr, d);
+  const dd<T> cci = dot3(br, ei, bi, er, -ci, d);
+  const dd<T> ecr = dot3(cr, br, ci, bi, -a, er);
+  const dd<T> eci = dot3(ci, br, -cr, bi, -a, ei);
   // det by Dot2 over the five products with the cofactors' high parts; the
   // products with their low parts are small and join the error accumulator.
-  float p, s, h, r, q;
+  T p, s, h, r, q;
   two_prod(a, ac.hi, p, s);
-  s = __fmaf_rn(a, ac.lo, s);
-  const float xs[4] = {br, bi, cr, ci};
-  const ff ys[4] = {bcr, bci, ccr, cci};
+  s = fma_rn(a, ac.lo, s);
+  const T xs[4] = {br, bi, cr, ci};
+  const dd<T> ys[4] = {bcr, bci, ccr, cci};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     two_prod(xs[k], ys[k].hi, h, r);
     two_sum(p, h, p, q);
-    s = __fadd_rn(s, __fadd_rn(q, r));
-    s = __fmaf_rn(xs[k], ys[k].lo, s);
+    s = add_rn(s, add_rn(q, r));
+    s = fma_rn(xs[k], ys[k].lo, s);
   }
-  float dhi, dlo;
+  T dhi, dlo;
   two_sum(p, s, dhi, dlo);
   det = dhi;
   // t ~ 1/(dhi + dlo): the correctly rounded reciprocal plus one Newton-type
   // correction using its exact residual 1 - dhi*t and the det's low part.
-  float t = __frcp_rn(dhi);
-  const float res = __fmaf_rn(-dhi, t, 1.0f);
-  t = __fmaf_rn(t, __fmaf_rn(-dlo, t, res), t);
-  const ff cof[9] = {ac, bcr, bci, ccr, cci, dc, ecr, eci, fc};
+  T t = rcp_rn(dhi);
+  const T res = fma_rn(-dhi, t, T(1));
+  t = fma_rn(t, fma_rn(-dlo, t, res), t);
+  const dd<T> cof[9] = {ac, bcr, bci, ccr, cci, dc, ecr, eci, fc};
 #pragma unroll
-  for (int k = 0; k < 9; ++k) w[k] = __fmaf_rn(cof[k].hi, t, __fmul_rn(cof[k].lo, t));
+  for (int k = 0; k < 9; ++k) w[k] = fma_rn(cof[k].hi, t, mul_rn(cof[k].lo, t));
 }
 
 // ---------------------------------------------------------------------------
@@ -183,7 +202,7 @@ __device__ __forceinline__ uint32_t pixel_inv_det(const float x[9], float w[9], 
   if (ALG == kChol) {
     cholesky_inv_det(x, w, det);
   } else if (ALG == kComp || ALG == kCompF64) {
-    adjugate_inv_det_comp(x, w, det);
+    adjugate_inv_det_comp<float>(x, w, det);
   } else {
     adjugate_inv_det<float>(x, w, det);
   }
@@ -191,16 +210,19 @@ __device__ __forceinline__ uint32_t pixel_inv_det(const float x[9], float w[9], 
   if (ALG == kPlainF64 || ALG == kCompF64) {
     // Hadamard ratio det/(a d f) in (0, 1] for positive definite Z; a small
     // ratio means cancellation ate the FP32 digits.  !(>) also catches NaN.
+    // The recompute is the compensated route in FP64: products of FP32 inputs
+    // and their Dot2 sums are exact enough that only the final FP32 rounding
+    // remains, even where the plain FP64 route would lose u64*cond^2.
     if (!(det > tau * (x[0] * x[5] * x[8]))) {
-      double xd[9], wd[9], dd;
+      double xd[9], wd[9], det64;
 #pragma unroll
       for (int k = 0; k < 9; ++k) xd[k] = (double)x[k];
-      adjugate_inv_det<double>(xd, wd, dd);
+      adjugate_inv_det_comp<double>(xd, wd, det64);
 #pragma unroll
       for (int k = 0; k < 9; ++k) w[k] = __double2float_rn(wd[k]);
-      det = __double2float_rn(dd);
+      det = __double2float_rn(det64);
       st |= ZINV_PIX_RECOMPUTED;
-      if (!(dd > 0.0) || !isfinite(dd)) st |= ZINV_PIX_NOT_PD;
+      if (!(det64 > 0.0) || !isfinite(det64)) st |= ZINV_PIX_NOT_PD;
       return st;
     }
   }
