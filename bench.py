@@ -242,6 +242,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sub-steps", type=int, default=50, help="steps per secondary path")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--multilook", type=int, default=1, help="also time the fused multilook")
+    ap.add_argument("--ml-rows", type=int, default=8192, help="multilook image height")
+    ap.add_argument("--wishart", type=int, default=1, help="also time the Wishart statistic")
+    ap.add_argument("--ws-rows", type=int, default=4096, help="Wishart image height")
     ap.add_argument("--rows", type=int, default=16384,
                     help="image height (16384 = the full workload; smaller for profiling)")
     args = ap.parse_args()
@@ -318,6 +322,49 @@ def main():
     del g_w, g_det, g_z
     sampler.stop()
 
+    # --- fused multilook (8192 x 8192 single-look, boxcar 3/5/7) ---------------
+    multilook = {}
+    if args.multilook:
+        wl = S.WORKLOADS["multilook_8k"]
+        if args.ml_rows != wl.H:
+            wl = S.scaled(wl, args.ml_rows, wl.W)
+        sl = G.image(wl)
+        ml_inv = torch.empty((9, wl.H, wl.W), device="cuda")
+        ml_det = torch.empty((wl.H, wl.W), device="cuda")
+        for win in wl.windows:
+            t = timed(lambda: zp.multilook_zinv_det(sl, win, None, zp.PLAIN, out=(ml_inv, ml_det)),
+                      sub, args.warmup, world)
+            gbs = 64 * wl.n / (t * 1e-3) / 1e9
+            multilook[f"win{win}"] = {"gpix_s": wl.n / (t * 1e-3) / 1e9, "ms": t, "gbs": gbs,
+                                      "frac_hbm": gbs / hbm_peak}
+        del sl, ml_inv, ml_det
+
+    # --- Wishart change statistic (two 4096 x 4096 dates, 7 x 7 window) -------
+    wishart = {}
+    if args.wishart:
+        ww = S.WORKLOADS["wishart_pair_4k"]
+        if args.ws_rows != ww.H:
+            ww = S.scaled(ww, args.ws_rows, ww.W)
+        s1, s2 = G.image(ww, 0), G.image(ww, 1)
+        wts = torch.full((49,), 1.0 / 49.0, device="cuda")
+        ws_buf = torch.empty(zp.wishart_workspace_bytes(ww.H, ww.W, 7), dtype=torch.uint8,
+                             device="cuda")
+        g1 = torch.ones((), dtype=torch.float64, device="cuda")
+        t_f = timed(lambda: zp.wishart_stat_fwd(s1, s2, wts, 7, ws=ws_buf), sub, args.warmup, world)
+        t_b = timed(lambda: zp.wishart_stat_bwd(s1, s2, wts, 7, g1, ws=ws_buf), sub, args.warmup,
+                    world)
+        # algorithmic FP32 work: the window sums, 2 dates x 49 taps x 9 channels FMA
+        # per pixel forward; the backward recomputes them and correlates as many
+        fl_f, fl_b = 2 * 2 * 49 * 9, 2 * 2 * 2 * 49 * 9
+        alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        for name, t, fl in (("forward", t_f, fl_f), ("backward", t_b, fl_b)):
+            tf = fl * ww.n / (t * 1e-3) / 1e12
+            wishart[name] = {"gpix_s": ww.n / (t * 1e-3) / 1e9, "ms": t, "tflops": tf,
+                             "frac_alu": tf / alu_peak,
+                             "gbs": 48 * ww.n / (t * 1e-3) / 1e9}
+        wishart["alu_peak_tflops"] = alu_peak
+        del s1, s2, ws_buf
+
     # --- end to end through the host-buffer entry point -----------------------
     e2e = None
     if args.e2e_steps > 0:
@@ -360,6 +407,8 @@ def main():
                          "kernel": "k_inv_det_vec4<plain>",
                          "algorithmic_bytes_per_launch": BYTES_FWD * n},
             "paths": paths,
+            "multilook_8k": multilook or None,
+            "wishart_pair_4k": wishart or None,
             "speedup_vs_cholesky": paths["cholesky"]["ms"] / ms,
             "e2e": e2e,
             "cpu_baseline": cpu,

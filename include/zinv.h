@@ -131,6 +131,65 @@ int zinv_det_bwd(const float* zinv, const float* det, int64_t n, int64_t ld,
                  void* stream);
 
 /*
+ * multilook_zinv_det -- fused multilook and inverse: for every pixel p of an
+ * H x W single-look image, the window covariance
+ *     Z(p) = (1/N) sum_{k in win x win} S(p+k) S(p+k)^H      (boxcar, N = win^2)
+ * (Eq. ZN, with S the column vector [S_HH, S_HV, S_VV]^T of §1), or
+ *     Z(p) = sum_k w_k S(p+k) S(p+k)^H                         (weighted window),
+ * with clamp-to-edge addressing at the image border, is formed on chip and
+ * inverted by Algorithm 2 as in zinv_det.  Z is never written to memory.
+ *
+ *   s        complex64 single-look planes (read only): component i of pixel
+ *            (y, x) at s[i*plane_ld + y*W + x] (interleaved re, im floats;
+ *            8-byte aligned), plane_ld >= H*W in complex elements.
+ *   win      window side: 3, 5 or 7 for the boxcar; any odd value up to 15
+ *            with weights.
+ *   weights  [win*win] device floats, row-major over (dy, dx) in [-r, r]^2,
+ *            r = (win-1)/2, or NULL for the boxcar.
+ *   zinv     [9][H*W] packed Z^-1 (plane stride H*W), det [H*W].
+ *   flags, tau, status, counts  as zinv_det.
+ */
+int multilook_zinv_det(const float* s, int64_t H, int64_t W, int64_t plane_ld, int win,
+                       const float* weights, float* zinv, float* det, uint32_t flags,
+                       float tau, uint8_t* status, int64_t* counts, void* stream);
+
+/*
+ * Wishart change statistic between two dates with a learnable window (the
+ * likelihood-ratio change test the paper lists among the consumers of det Z and
+ * Z^-1, §1).  For every pixel p of two co-registered H x W single-look images
+ * and t = 1, 2:
+ *     Z_t(p) = sum_k w_k S_t(p+k) S_t(p+k)^H      (win x win window, clamp-to-edge)
+ *     q(p)   = ln det Z1 + ln det Z2 - 2 ln det((Z1 + Z2)/2)   (<= 0; 0 iff Z1 = Z2)
+ *     L      = sum_p q(p).
+ * Determinants and inverses follow Algorithm 2 with compensated (Dot2)
+ * arithmetic.  Deterministic: per-tile FP64 partial sums in the workspace,
+ * added in a fixed order (no float atomics); repeated calls give the same bits.
+ *
+ *   s1, s2    complex64 single-look images, layout as multilook_zinv_det.
+ *   win       3, 5 or 7.
+ *   weights   [win*win] device floats, row-major over (dy, dx), r = (win-1)/2;
+ *             positive weights keep Z positive definite (needs >= 3 distinct looks).
+ *   ws, ws_bytes  caller-owned device workspace of at least
+ *             wishart_workspace_bytes(H, W, win) bytes (8-byte aligned); its
+ *             contents are scratch, overwritten by every call.
+ *
+ * wishart_stat_fwd: q_map [H*W] device floats or NULL; d_loss: one device double,
+ *   overwritten with L.  A window whose Z is not positive definite gives NaN.
+ * wishart_stat_bwd: recomputes every Z_t from s (nothing is kept from the
+ *   forward) and writes grad_weights[k] = g * dL/dw_k (win*win device floats),
+ *   g = *d_grad_loss (a device double; NULL means 1), where
+ *     dL/dw_k = sum_p sum_t S_t(p+k)^H M_t(p) S_t(p+k),
+ *     M_t = Z_t^-1 - 2 (Z1 + Z2)^-1.
+ */
+size_t wishart_workspace_bytes(int64_t H, int64_t W, int win);
+int wishart_stat_fwd(const float* s1, const float* s2, int64_t H, int64_t W, int64_t plane_ld,
+                     int win, const float* weights, float* q_map, double* d_loss, void* ws,
+                     size_t ws_bytes, void* stream);
+int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int64_t W, int64_t plane_ld,
+                     int win, const float* weights, const double* d_grad_loss,
+                     float* grad_weights, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * zinv_det_host -- zinv_det over HOST buffers, streamed through the GPU in
  * chunks (the paper's §4.3: data larger than device memory is fed in pieces,
  * processed and pulled back).  Copies in, kernel and copies out of successive

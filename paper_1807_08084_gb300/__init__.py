@@ -186,6 +186,120 @@ def zinv_det_bwd(zinv: torch.Tensor, det: torch.Tensor, g_zinv=None, g_det=None,
     return g_z
 
 
+def _slc(s: torch.Tensor, name: str = "s"):
+    """(H, W, plane_ld) of a complex64 [3, H, W] CUDA tensor with contiguous rows."""
+    if not s.is_cuda or s.dtype != torch.complex64:
+        raise ValueError(f"{name} must be a complex64 CUDA tensor")
+    if s.dim() != 3 or s.shape[0] != 3:
+        raise ValueError(f"{name} must have shape [3, H, W]")
+    H, W = s.shape[1], s.shape[2]
+    if s.stride(2) != 1 or (H > 1 and s.stride(1) != W):
+        raise ValueError(f"{name} rows must be contiguous ([3, H, W] with strides (plane, W, 1))")
+    return H, W, max(s.stride(0), H * W)
+
+
+def multilook_zinv_det(s: torch.Tensor, win: int = 7, weights: torch.Tensor | None = None,
+                       flags: int = PLAIN, tau: float = DEFAULT_TAU, want_status: bool = False,
+                       want_counts: bool = False, out: tuple | None = None):
+    """Fused multilook (boxcar mean, or the weighted window) + Algorithm 2.
+
+    s: complex64 [3, H, W] single-look vectors; returns (Z^-1 [9, H, W], det [H, W])
+    [+ status] [+ counts]; Z itself is never materialised."""
+    lib = load()
+    H, W, pld = _slc(s)
+    if weights is not None:
+        if (not weights.is_cuda or weights.dtype != torch.float32 or weights.numel() != win * win
+                or not weights.is_contiguous()):
+            raise ValueError("weights must be a contiguous float32 CUDA tensor of win*win values")
+    if out is None:
+        zinv = torch.empty((9, H, W), dtype=torch.float32, device=s.device)
+        det = torch.empty((H, W), dtype=torch.float32, device=s.device)
+    else:
+        zinv, det = out
+    status = torch.empty((H, W), dtype=torch.uint8, device=s.device) if want_status else None
+    counts = torch.empty(2, dtype=torch.int64, device=s.device) if want_counts else None
+    with torch.cuda.device(s.device):
+        rc = lib.multilook_zinv_det(_ptr(s), H, W, pld, int(win), _ptr(weights), _ptr(zinv),
+                                    _ptr(det), int(flags), float(tau), _ptr(status), _ptr(counts),
+                                    _stream(s.device))
+    _check(rc, "multilook_zinv_det")
+    res = (zinv, det)
+    if want_status:
+        res += (status,)
+    if want_counts:
+        res += (counts,)
+    return res
+
+
+def wishart_workspace_bytes(H: int, W: int, win: int) -> int:
+    return int(load().wishart_workspace_bytes(int(H), int(W), int(win)))
+
+
+def _wishart_common(s1, s2, weights, win, ws):
+    H, W, pld = _slc(s1, "s1")
+    H2, W2, pld2 = _slc(s2, "s2")
+    if (H, W) != (H2, W2) or pld != pld2 or s1.device != s2.device:
+        raise ValueError("s1 and s2 must have the same shape, plane stride and device")
+    if (not weights.is_cuda or weights.dtype != torch.float32 or weights.numel() != win * win
+            or not weights.is_contiguous()):
+        raise ValueError("weights must be a contiguous float32 CUDA tensor of win*win values")
+    need = wishart_workspace_bytes(H, W, win)
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=s1.device)
+    elif not ws.is_cuda or ws.dtype != torch.uint8 or ws.numel() < need:
+        raise ValueError(f"ws must be a uint8 CUDA tensor of at least {need} bytes")
+    return H, W, pld, ws
+
+
+def wishart_stat_fwd(s1: torch.Tensor, s2: torch.Tensor, weights: torch.Tensor, win: int = 7,
+                     want_map: bool = False, ws: torch.Tensor | None = None):
+    """L = sum_p [ln det Z1 + ln det Z2 - 2 ln det((Z1+Z2)/2)] (float64 0-dim tensor)
+    [+ the per-pixel q map [H, W]]."""
+    lib = load()
+    H, W, pld, ws = _wishart_common(s1, s2, weights, win, ws)
+    loss = torch.empty((), dtype=torch.float64, device=s1.device)
+    q = torch.empty((H, W), dtype=torch.float32, device=s1.device) if want_map else None
+    with torch.cuda.device(s1.device):
+        rc = lib.wishart_stat_fwd(_ptr(s1), _ptr(s2), H, W, pld, int(win), _ptr(weights),
+                                  _ptr(q), _ptr(loss), _ptr(ws), ws.numel(), _stream(s1.device))
+    _check(rc, "wishart_stat_fwd")
+    return (loss, q) if want_map else loss
+
+
+def wishart_stat_bwd(s1: torch.Tensor, s2: torch.Tensor, weights: torch.Tensor, win: int = 7,
+                     grad_loss: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+    """g * dL/dw (float32, shaped like weights); grad_loss a float64 CUDA scalar or None (1)."""
+    lib = load()
+    H, W, pld, ws = _wishart_common(s1, s2, weights, win, ws)
+    if grad_loss is not None:
+        grad_loss = grad_loss.to(device=s1.device, dtype=torch.float64).contiguous()
+    gw = torch.empty_like(weights)
+    with torch.cuda.device(s1.device):
+        rc = lib.wishart_stat_bwd(_ptr(s1), _ptr(s2), H, W, pld, int(win), _ptr(weights),
+                                  _ptr(grad_loss), _ptr(gw), _ptr(ws), ws.numel(),
+                                  _stream(s1.device))
+    _check(rc, "wishart_stat_bwd")
+    return gw
+
+
+class WishartStat(torch.autograd.Function):
+    """loss = WishartStat.apply(s1, s2, weights, win): the change statistic with a
+    learnable window; backward recomputes Z from s1, s2 in the kernel and returns
+    the weights' gradient only (the images are data)."""
+
+    @staticmethod
+    def forward(ctx, s1, s2, weights, win: int = 7):
+        ctx.save_for_backward(s1, s2, weights)
+        ctx.win = win
+        return wishart_stat_fwd(s1, s2, weights.contiguous(), win)
+
+    @staticmethod
+    def backward(ctx, g):
+        s1, s2, weights = ctx.saved_tensors
+        gw = wishart_stat_bwd(s1, s2, weights.contiguous(), ctx.win, g.reshape(()))
+        return None, None, gw.reshape(weights.shape), None
+
+
 def zinv_det_host_workspace_bytes(chunk: int) -> int:
     return int(load().zinv_det_host_workspace_bytes(int(chunk)))
 

@@ -1,0 +1,403 @@
+// multilook.cu -- fused multilook + inverse + determinant.
+//
+// Per output pixel p the window covariance Z(p) = (1/N) sum_{k in win} s s^H
+// (Eq. ZN, boxcar, N = win^2) or sum_k w_k s s^H (weighted window) is formed in
+// shared memory and registers from the single-look vectors s, then inverted by
+// Algorithm 2 (same per-pixel code and flags as zinv_det).  Z never reaches HBM:
+// 24 B are read and 40 B written per pixel.
+//
+// Boxcar: persistent CTAs walk strip segments (kTW columns x kSeg rows) down
+// the image in steps of kCH output rows.  Per step:
+//   - cp.async brings the next step's kCH raw input rows (plus the r-column
+//     halo, clamp-to-edge) into the other half of a double buffer, so the copy
+//     of step k+1 overlaps the arithmetic of step k;
+//   - phase H: the nine channel products |s0|^2, Re/Im s0 conj s1, Re/Im s0 conj
+//     s2, |s1|^2, Re/Im s1 conj s2, |s2|^2 of each new row and their horizontal
+//     window sums (four adjacent outputs per thread) go into a ring of kRing
+//     rows in shared memory;
+//   - phase V: vertical window sums over the ring (four rows per thread), scale
+//     by 1/N, invert, store (warp-contiguous along x).
+// Each input row is loaded once per strip (plus 2r rows at a segment start and
+// 2r halo columns): ~1.1x the ideal read traffic.  The weighted window uses a
+// simpler tiled kernel.
+#include "common.cuh"
+#include "pixel.cuh"
+
+namespace zinv {
+
+namespace {
+
+constexpr int kMlThreads = 256;
+constexpr int kTW = 64;  // output tile width
+constexpr int kTH = 16;  // output tile height
+
+struct MlArgs {
+  const float2* s;
+  int64_t H, W, plane_ld;
+  float* zinv;
+  float* det;
+  float tau;
+  uint8_t* status;
+  unsigned long long* counts;
+  const float* weights;  // device, win*win, or null (boxcar)
+  int win;
+};
+
+__device__ __forceinline__ int64_t clamp64(int64_t v, int64_t hi) {
+  return v < 0 ? 0 : (v > hi ? hi : v);
+}
+
+// The nine channels of s s^H in packed order: a, Re b, Im b, Re c, Im c, d,
+// Re e, Im e, f with b = s0 conj s1, c = s0 conj s2, e = s1 conj s2.
+__device__ __forceinline__ void channels(float2 s0, float2 s1, float2 s2, float p[9]) {
+  p[0] = s0.x * s0.x + s0.y * s0.y;
+  p[1] = s0.x * s1.x + s0.y * s1.y;
+  p[2] = s0.y * s1.x - s0.x * s1.y;
+  p[3] = s0.x * s2.x + s0.y * s2.y;
+  p[4] = s0.y * s2.x - s0.x * s2.y;
+  p[5] = s1.x * s1.x + s1.y * s1.y;
+  p[6] = s1.x * s2.x + s1.y * s2.y;
+  p[7] = s1.y * s2.x - s1.x * s2.y;
+  p[8] = s2.x * s2.x + s2.y * s2.y;
+}
+
+// Sums of L = 2R+1 consecutive values for four adjacent outputs:
+// out[j] = v[j] + ... + v[j+L-1], j = 0..3, sharing the common middle.
+template <int R>
+__device__ __forceinline__ void window4(const float* v, float out[4]) {
+  constexpr int L = 2 * R + 1;
+  if constexpr (L == 3) {
+    const float a = v[1] + v[2], b = v[3] + v[4];
+    out[0] = v[0] + a;
+    out[1] = a + v[3];
+    out[2] = v[2] + b;
+    out[3] = b + v[5];
+  } else {
+    float core = v[3];
+#pragma unroll
+    for (int k = 4; k < L; ++k) core += v[k];
+    const float a = v[1] + v[2], b = v[L] + v[L + 1];
+    out[0] = core + (v[0] + a);
+    out[1] = core + (a + v[L]);
+    out[2] = core + (v[2] + b);
+    out[3] = core + (b + v[L + 2]);
+  }
+}
+
+template <int ALG, bool STAT>
+__device__ __forceinline__ void finish_pixel(const MlArgs& a, int64_t gy, int64_t gx, float z[9],
+                                             uint32_t& c0, uint32_t& c1) {
+  const int64_t n = a.H * a.W;
+  const int64_t p = gy * a.W + gx;
+  float w[9], dt;
+  const uint32_t st = pixel_inv_det<ALG>(z, w, dt, a.tau);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) __stcs(a.zinv + k * n + p, w[k]);
+  __stcs(a.det + p, dt);
+  if (STAT) {
+    if (a.status) a.status[p] = (uint8_t)st;
+    c0 += st & ZINV_PIX_NOT_PD;
+    c1 += (st & ZINV_PIX_RECOMPUTED) >> 1;
+  }
+}
+
+// Phase 1, shared by the boxcar and the weighted kernels.  Each thread first
+// issues the loads of all its staged pixels (one memory round trip per tile),
+// then forms their products and writes them to shared memory.
+template <int R, int SH, int SWP, int SW>
+__device__ __forceinline__ void stage_products(const MlArgs& a, int64_t ty0, int64_t tx0,
+                                               float* P) {
+  constexpr int KMAX = (SH * SW + kMlThreads - 1) / kMlThreads;
+  float2 v[KMAX][3];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int i = threadIdx.x + k * kMlThreads;
+    if (i < SH * SW) {
+      const int iy = i / SW, ix = i - (i / SW) * SW;
+      const int64_t gy = clamp64(ty0 - R + iy, a.H - 1);
+      const int64_t gx = clamp64(tx0 - R + ix, a.W - 1);
+      const int64_t q = gy * a.W + gx;
+      v[k][0] = __ldg(a.s + q);
+      v[k][1] = __ldg(a.s + a.plane_ld + q);
+      v[k][2] = __ldg(a.s + 2 * a.plane_ld + q);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int i = threadIdx.x + k * kMlThreads;
+    if (i < SH * SW) {
+      const int iy = i / SW, ix = i - (i / SW) * SW;
+      float p[9];
+      channels(v[k][0], v[k][1], v[k][2], p);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) P[(c * SH + iy) * SWP + ix] = p[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Boxcar strip walker
+// ---------------------------------------------------------------------------
+constexpr int kSThreads = 128;
+constexpr int kCH = 8;      // output rows per step
+constexpr int kRing = 16;   // ring rows of horizontal sums (>= kCH + 2r)
+constexpr int kSeg = 256;   // rows per strip segment
+
+template <int R>
+struct Strip {
+  static constexpr int SW = kTW + 2 * R;                    // input columns per row
+  static constexpr size_t raw_f2 = 2 * 3 * kCH * SW;        // float2 [2][3][kCH][SW]
+  static constexpr size_t ring_f = 9 * kRing * kTW;         // float [9][kRing][kTW]
+  static constexpr size_t smem = raw_f2 * sizeof(float2) + ring_f * sizeof(float);
+};
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Issues the copies of `rows` input rows starting at relative row rr0 of the
+// segment (absolute row y_begin - R + rr, clamped) into buffer `buf`.
+template <int R>
+__device__ __forceinline__ void load_rows(const MlArgs& a, float2* raw, int buf, int64_t y_begin,
+                                          int64_t x0, int rr0, int rows) {
+  using T = Strip<R>;
+  const int n = 3 * rows * T::SW;
+  for (int i = threadIdx.x; i < n; i += kSThreads) {
+    const int p = i / (rows * T::SW);
+    const int rem = i - p * (rows * T::SW);
+    const int r = rem / T::SW, ix = rem - r * T::SW;
+    const int64_t gy = clamp64(y_begin - R + rr0 + r, a.H - 1);
+    const int64_t gx = clamp64(x0 - R + ix, a.W - 1);
+    cp_async8(raw + ((buf * 3 + p) * kCH + r) * T::SW + ix, a.s + p * a.plane_ld + gy * a.W + gx);
+  }
+}
+
+template <int R, int ALG, bool STAT>
+__global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
+  using T = Strip<R>;
+  constexpr int SW = T::SW;
+  extern __shared__ __align__(16) float smem[];
+  float2* raw = reinterpret_cast<float2*>(smem);
+  float* ring = smem + 2 * T::raw_f2;
+  const int64_t strips_x = (a.W + kTW - 1) / kTW;
+  const int64_t segs = (a.H + kSeg - 1) / kSeg;
+  const int64_t units = strips_x * segs;
+  const float invN = 1.0f / (float)((2 * R + 1) * (2 * R + 1));
+  uint32_t c0 = 0, c1 = 0;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t x0 = (u % strips_x) * kTW;
+    const int64_t y_begin = (u / strips_x) * kSeg;
+    const int64_t y_end = (y_begin + kSeg < a.H) ? y_begin + kSeg : a.H;
+    const int out_rows = (int)(y_end - y_begin);
+    // job 0: the 2R rows above the first output row's window centre; job j >= 1:
+    // input rows 2R + (j-1) kCH .. + kCH (relative), output rows (j-1) kCH .. + kCH.
+    const int jobs = 1 + (out_rows + kCH - 1) / kCH;
+    __syncthreads();  // the previous unit is done with raw and ring
+    load_rows<R>(a, raw, 0, y_begin, x0, 0, 2 * R);
+    cp_async_commit();
+    for (int j = 0; j < jobs; ++j) {
+      const int rr0 = j == 0 ? 0 : 2 * R + (j - 1) * kCH;
+      const int rows = j == 0 ? 2 * R : kCH;
+      if (j + 1 < jobs) {
+        load_rows<R>(a, raw, (j + 1) & 1, y_begin, x0, 2 * R + j * kCH, kCH);
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      // phase H: products and horizontal sums of the job's rows -> ring
+      const float2* rb = raw + (size_t)((j & 1) * 3) * kCH * SW;
+      for (int i = threadIdx.x; i < rows * (kTW / 4); i += kSThreads) {
+        const int r = i % rows, xr = (i / rows) * 4;
+        float pv[9][4 + 2 * R];
+#pragma unroll
+        for (int k = 0; k < 4 + 2 * R; ++k) {
+          const float2 s0 = rb[(0 * kCH + r) * SW + xr + k];
+          const float2 s1 = rb[(1 * kCH + r) * SW + xr + k];
+          const float2 s2 = rb[(2 * kCH + r) * SW + xr + k];
+          float p[9];
+          channels(s0, s1, s2, p);
+#pragma unroll
+          for (int c = 0; c < 9; ++c) pv[c][k] = p[c];
+        }
+        const int slot = (rr0 + r) % kRing;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          float o[4];
+          window4<R>(pv[c], o);
+          *reinterpret_cast<float4*>(ring + (c * kRing + slot) * kTW + xr) =
+              make_float4(o[0], o[1], o[2], o[3]);
+        }
+      }
+      __syncthreads();
+      if (j == 0) continue;
+      // phase V: output rows (j-1) kCH .. of this job
+      const int oy0 = (j - 1) * kCH;
+      const int orows = (out_rows - oy0) < kCH ? (out_rows - oy0) : kCH;
+      for (int i = threadIdx.x; i < kTW * ((orows + 3) / 4); i += kSThreads) {
+        const int x = i % kTW, yq = (i / kTW) * 4;
+        float z[4][9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          float v[4 + 2 * R];
+#pragma unroll
+          for (int k = 0; k < 4 + 2 * R; ++k)
+            v[k] = ring[(c * kRing + (oy0 + yq + k) % kRing) * kTW + x];
+          float o[4];
+          window4<R>(v, o);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) z[q][c] = o[q] * invN;
+        }
+        const int64_t gx = x0 + x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int oy = oy0 + yq + q;
+          if (oy < out_rows && gx < a.W) finish_pixel<ALG, STAT>(a, y_begin + oy, gx, z[q], c0, c1);
+        }
+      }
+    }
+  }
+  if (STAT && a.counts) add_counts(a.counts, c0, c1);
+}
+
+// Weighted (or any odd window up to kMaxWin) covariance: Z(p) = sum_k w_k P(p+k),
+// one output per work item over all taps.  Weights in shared memory.
+constexpr int kMaxWin = 15;
+constexpr int kWR = (kMaxWin - 1) / 2;
+constexpr int kWSH = kTH + 2 * kWR, kWSW = kTW + 2 * kWR, kWSWP = (kWSW + 3) / 4 * 4;
+constexpr size_t kWSmem = (9 * kWSH * kWSWP + kMaxWin * kMaxWin) * sizeof(float);
+
+template <int ALG, bool STAT>
+__global__ void __launch_bounds__(kMlThreads) k_multilook_weighted(MlArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  float* P = smem;
+  float* wsh = smem + 9 * kWSH * kWSWP;
+  const int r = (a.win - 1) / 2;
+  for (int i = threadIdx.x; i < a.win * a.win; i += blockDim.x) wsh[i] = a.weights[i];
+  const int64_t tiles_x = (a.W + kTW - 1) / kTW;
+  const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
+  uint32_t c0 = 0, c1 = 0;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t ty0 = (t / tiles_x) * kTH, tx0 = (t % tiles_x) * kTW;
+    // stage with the maximal halo; taps only reach r <= kWR of it
+    stage_products<kWR, kWSH, kWSWP, kWSW>(a, ty0, tx0, P);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTW * kTH; i += blockDim.x) {
+      const int x = i % kTW, y = i / kTW;
+      float z[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) z[c] = 0.0f;
+      for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+          const float wk = wsh[(dy + r) * a.win + (dx + r)];
+          const int iy = y + kWR + dy, ix = x + kWR + dx;
+#pragma unroll
+          for (int c = 0; c < 9; ++c) z[c] = fmaf(wk, P[(c * kWSH + iy) * kWSWP + ix], z[c]);
+        }
+      const int64_t gy = ty0 + y, gx = tx0 + x;
+      if (gy < a.H && gx < a.W) finish_pixel<ALG, STAT>(a, gy, gx, z, c0, c1);
+    }
+    __syncthreads();
+  }
+  if (STAT && a.counts) add_counts(a.counts, c0, c1);
+}
+
+template <typename K>
+int launch_ml(K kernel, size_t smem, const MlArgs& a, cudaStream_t s, const DeviceInfo& di) {
+  static_assert(sizeof(K) > 0, "");
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return ZINV_ERR_LAUNCH;
+  }
+  const int64_t tiles = ((a.W + kTW - 1) / kTW) * ((a.H + kTH - 1) / kTH);
+  const int64_t blocks = grid_blocks((const void*)kernel, kMlThreads, smem, tiles * kMlThreads, di);
+  kernel<<<(unsigned)blocks, kMlThreads, smem, s>>>(a);
+  return launch_status();
+}
+
+template <typename K>
+int launch_strip(K kernel, size_t smem, const MlArgs& a, cudaStream_t s, const DeviceInfo& di) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return ZINV_ERR_LAUNCH;
+  }
+  const int64_t units = ((a.W + kTW - 1) / kTW) * ((a.H + kSeg - 1) / kSeg);
+  const int64_t blocks = grid_blocks((const void*)kernel, kSThreads, smem, units * kSThreads, di);
+  kernel<<<(unsigned)blocks, kSThreads, smem, s>>>(a);
+  return launch_status();
+}
+
+template <int ALG, bool STAT>
+int dispatch_ml(const MlArgs& a, cudaStream_t s, const DeviceInfo& di) {
+  if (a.weights)
+    return launch_ml(k_multilook_weighted<ALG, STAT>, kWSmem, a, s, di);
+  switch (a.win) {
+    case 3: return launch_strip(k_multilook_strip<1, ALG, STAT>, Strip<1>::smem, a, s, di);
+    case 5: return launch_strip(k_multilook_strip<2, ALG, STAT>, Strip<2>::smem, a, s, di);
+    case 7: return launch_strip(k_multilook_strip<3, ALG, STAT>, Strip<3>::smem, a, s, di);
+  }
+  return ZINV_ERR_ARG;
+}
+
+template <int ALG>
+int dispatch_ml_stat(const MlArgs& a, cudaStream_t s, const DeviceInfo& di) {
+  if (a.status || a.counts) return dispatch_ml<ALG, true>(a, s, di);
+  return dispatch_ml<ALG, false>(a, s, di);
+}
+
+}  // namespace
+
+int alg_from_flags(uint32_t flags);
+
+}  // namespace zinv
+
+extern "C" int multilook_zinv_det(const float* s, int64_t H, int64_t W, int64_t plane_ld,
+                                  int win, const float* weights, float* zinv, float* det,
+                                  uint32_t flags, float tau, uint8_t* status, int64_t* counts,
+                                  void* stream) {
+  using namespace zinv;
+  const int alg = alg_from_flags(flags);
+  if (alg < 0 || H < 0 || W < 0 || (W > 0 && H > kMaxLd / W)) return ZINV_ERR_ARG;
+  if (!(tau >= 0.0f) || isinf(tau)) return ZINV_ERR_ARG;
+  if (plane_ld < H * W || plane_ld > kMaxLd) return ZINV_ERR_ARG;
+  if (weights ? (win < 1 || win > kMaxWin || win % 2 == 0) : (win != 3 && win != 5 && win != 7))
+    return ZINV_ERR_ARG;
+  const int64_t n = H * W;
+  if (n > 0 && (!s || !zinv || !det)) return ZINV_ERR_ARG;
+  if (!aligned(s, 8) || !aligned(zinv, 4) || !aligned(det, 4) || !aligned(counts, 8) ||
+      !aligned(weights, 4))
+    return ZINV_ERR_ARG;
+  DeviceInfo di;
+  int rc = device_info(&di);
+  if (rc != ZINV_OK) return rc;
+  if (n > 0 && (!device_accessible(s) || !device_accessible(zinv) || !device_accessible(det)))
+    return ZINV_ERR_ARG;
+  if ((weights && !device_accessible(weights)) || (status && !device_accessible(status)) ||
+      (counts && !device_accessible(counts)))
+    return ZINV_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto* cnt = reinterpret_cast<unsigned long long*>(counts);
+  if (cnt && cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess)
+    return ZINV_ERR_LAUNCH;
+  if (n == 0) return ZINV_OK;
+  MlArgs a{reinterpret_cast<const float2*>(s), H, W, plane_ld, zinv, det, tau, status, cnt,
+           weights, win};
+  switch (alg) {
+    case kPlain: return dispatch_ml_stat<kPlain>(a, st, di);
+    case kComp: return dispatch_ml_stat<kComp>(a, st, di);
+    case kPlainF64: return dispatch_ml_stat<kPlainF64>(a, st, di);
+    case kCompF64: return dispatch_ml_stat<kCompF64>(a, st, di);
+  }
+  return ZINV_ERR_ARG;
+}

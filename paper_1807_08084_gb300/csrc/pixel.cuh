@@ -143,6 +143,34 @@ __device__ __forceinline__ void adjugate_inv_det_comp(const T x[9], T w[9], T& d
   for (int k = 0; k < 9; ++k) w[k] = fma_rn(cof[k].hi, t, mul_rn(cof[k].lo, t));
 }
 
+// det alone by the compensated route: the first-column cofactors a_c, b_c, c_c
+// (Eq. adjoint_elements) and Eq. detr, all by Dot2; returned as hi + lo.
+template <typename T>
+__device__ __forceinline__ dd<T> det_comp(const T x[9]) {
+  const T a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
+  const T d = x[5], er = x[6], ei = x[7], f = x[8];
+  const dd<T> ac = dot3(d, f, -er, er, -ei, ei);
+  const dd<T> bcr = dot3(cr, er, ci, ei, -br, f);
+  const dd<T> bci = dot3(ci, er, -cr, ei, -bi, f);
+  const dd<T> ccr = dot3(br, er, -bi, ei, -cr, d);
+  const dd<T> cci = dot3(br, ei, bi, er, -ci, d);
+  T p, s, h, r, q;
+  two_prod(a, ac.hi, p, s);
+  s = fma_rn(a, ac.lo, s);
+  const T xs[4] = {br, bi, cr, ci};
+  const dd<T> ys[4] = {bcr, bci, ccr, cci};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    two_prod(xs[k], ys[k].hi, h, r);
+    two_sum(p, h, p, q);
+    s = add_rn(s, add_rn(q, r));
+    s = fma_rn(xs[k], ys[k].lo, s);
+  }
+  dd<T> out;
+  two_sum(p, s, out.hi, out.lo);
+  return out;
+}
+
 // ---------------------------------------------------------------------------
 // Alg. 1 (§2.2), Cholesky route, FP32 with correctly rounded sqrt and
 // reciprocal.  Z = L L^H, L lower triangular with real positive diagonal:

@@ -1,0 +1,152 @@
+"""GPU parity of the Wishart change statistic (wishart_stat_fwd / _bwd and the
+WishartStat autograd Function) against the FP64 oracle, through the C ABI.
+
+The GPU forms Z_t in FP32 (49 weighted products per entry for 7 x 7), then
+takes log-dets by the compensated route.  Per pixel, |q_gpu - q_oracle| is
+bounded by the FP32 rounding of Z (componentwise <= g u sqrt(Z_ii Z_jj)), which
+moves ln det by <= 3 g u cond(C) with C the unit-diagonal (correlation) form of
+Z, plus the logf roundings; the tests use Q_TOL per pixel and relative bounds
+for the sums that follow from it.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1807_08084_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+Q_ABS = 2e-4     # per-pixel q, absolute (|q| is O(1..10) on changed pixels)
+G_REL = 1e-4     # weight gradient, relative to its largest component
+
+
+def pair(H, W, seed_shift=0):
+    w = S.scaled(S.WORKLOADS["wishart_pair_4k"], H, W)
+    return w, w.image(0), w.image(1)
+
+
+def weights(win, seed=0):
+    rng = np.random.default_rng(seed + win)
+    return rng.uniform(0.5, 1.5, win * win).astype(np.float32) / (win * win)
+
+
+@pytest.mark.parametrize("win", [3, 5, 7])
+@pytest.mark.parametrize("shape", [(37, 70), (8, 64), (21, 5)])
+def test_forward_and_backward_small(zlib, orc, win, shape):
+    H, W = shape
+    w, s1_np, s2_np = pair(H, W)
+    wt = weights(win)
+    s1, s2 = torch.from_numpy(s1_np).cuda(), torch.from_numpy(s2_np).cuda()
+    wd = torch.from_numpy(wt).cuda()
+    loss, q = zlib.wishart_stat_fwd(s1, s2, wd, win, want_map=True)
+    g = zlib.wishart_stat_bwd(s1, s2, wd, win)
+    torch.cuda.synchronize()
+    ref_loss, ref_q = orc.wishart_fwd(s1_np, s2_np, win, wt, want_map=True)
+    ref_g = orc.wishart_bwd(s1_np, s2_np, win, wt, 1.0)
+    dq = np.abs(q.cpu().numpy().ravel() - ref_q)
+    assert dq.max() <= Q_ABS, f"max |dq| {dq.max():.3e}"
+    assert abs(float(loss) - ref_loss) <= Q_ABS * H * W
+    np.testing.assert_allclose(float(loss), q.double().sum().item(), rtol=1e-12, atol=1e-9)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.abs(gg - ref_g).max() <= G_REL * np.abs(ref_g).max(), (
+        f"grad rel err {np.abs(gg - ref_g).max() / np.abs(ref_g).max():.3e}")
+    # bit-exact repeat
+    loss2 = zlib.wishart_stat_fwd(s1, s2, wd, win)
+    g2 = zlib.wishart_stat_bwd(s1, s2, wd, win)
+    torch.cuda.synchronize()
+    assert float(loss2) == float(loss) and torch.equal(g2, g)
+
+
+def test_no_change_gives_zero(zlib):
+    w, s1_np, _ = pair(40, 90)
+    s1 = torch.from_numpy(s1_np).cuda()
+    wd = torch.from_numpy(weights(7)).cuda()
+    loss, q = zlib.wishart_stat_fwd(s1, s1, wd, 7, want_map=True)
+    torch.cuda.synchronize()
+    assert q.abs().max().item() < 1e-5
+    assert abs(float(loss)) < 1e-5 * q.numel()
+
+
+def test_gradient_vs_fp64_finite_differences(zlib, orc):
+    """64 x 64 crop: the GPU's analytic weight gradient against FP64 central
+    differences of the oracle's forward."""
+    w, s1_np, s2_np = pair(64, 64)
+    wt = weights(7, seed=3).astype(np.float64)
+    g = zlib.wishart_stat_bwd(torch.from_numpy(s1_np).cuda(), torch.from_numpy(s2_np).cuda(),
+                              torch.from_numpy(wt.astype(np.float32)).cuda(), 7)
+    torch.cuda.synchronize()
+    w32 = wt.astype(np.float32).astype(np.float64)
+    fd = np.empty(49)
+    for k in range(49):
+        h = 1e-5 * max(1.0, abs(w32[k]))
+        wp, wm = w32.copy(), w32.copy()
+        wp[k] += h
+        wm[k] -= h
+        fd[k] = (orc.wishart_fwd(s1_np, s2_np, 7, wp) - orc.wishart_fwd(s1_np, s2_np, 7, wm)) / (2 * h)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.abs(gg - fd).max() <= G_REL * np.abs(fd).max(), (
+        f"FD rel err {np.abs(gg - fd).max() / np.abs(fd).max():.3e}")
+
+
+def test_invariants(zlib):
+    """Euler (L homogeneous of degree 0 in w), date swap, upstream scaling, autograd."""
+    import paper_1807_08084_gb300 as zp
+    w, s1_np, s2_np = pair(96, 160)
+    s1, s2 = torch.from_numpy(s1_np).cuda(), torch.from_numpy(s2_np).cuda()
+    wd = torch.from_numpy(weights(7, seed=5)).cuda()
+    g = zlib.wishart_stat_bwd(s1, s2, wd, 7)
+    l12 = zlib.wishart_stat_fwd(s1, s2, wd, 7)
+    l21 = zlib.wishart_stat_fwd(s2, s1, wd, 7)
+    g21 = zlib.wishart_stat_bwd(s2, s1, wd, 7)
+    g_scaled = zlib.wishart_stat_bwd(s1, s2, wd, 7, torch.tensor(-2.5, dtype=torch.float64))
+    torch.cuda.synchronize()
+    gd = g.double()
+    assert abs(float((gd * wd.double()).sum())) <= 1e-4 * float(gd.abs().max() * wd.abs().max()) * 49
+    assert abs(float(l12) - float(l21)) <= 1e-6 * abs(float(l12))
+    assert torch.allclose(g, g21, rtol=1e-4, atol=1e-4 * float(g.abs().max()))
+    assert torch.allclose(g_scaled, -2.5 * g, rtol=1e-6, atol=0)
+    # scaling all weights leaves L unchanged (degree-0 homogeneity)
+    l_scaled = zlib.wishart_stat_fwd(s1, s2, wd * 4.0, 7)
+    torch.cuda.synchronize()
+    assert abs(float(l_scaled) - float(l12)) <= 1e-5 * abs(float(l12))
+    # autograd Function
+    wp = wd.clone().requires_grad_()
+    loss = zp.WishartStat.apply(s1, s2, wp, 7)
+    (3.0 * loss).backward()
+    torch.cuda.synchronize()
+    assert torch.allclose(wp.grad, 3.0 * g, rtol=1e-6, atol=0)
+
+
+def test_full_size_pair(zlib, orc):
+    """Both 4096 x 4096 dates generated on the GPU; forward and backward in the
+    benchmark's launch configuration.  Crops of the q map against the oracle,
+    the loss as the sum of the q map, determinism, Euler invariant."""
+    from paper_1807_08084_gb300.synth import gpu as G
+    w = S.WORKLOADS["wishart_pair_4k"]
+    s1, s2 = G.image(w, 0), G.image(w, 1)
+    wd = torch.full((49,), 1 / 49, device="cuda")
+    loss, q = zlib.wishart_stat_fwd(s1, s2, wd, 7, want_map=True)
+    g = zlib.wishart_stat_bwd(s1, s2, wd, 7)
+    loss_b = zlib.wishart_stat_fwd(s1, s2, wd, 7)
+    g_b = zlib.wishart_stat_bwd(s1, s2, wd, 7)
+    torch.cuda.synchronize()
+    assert float(loss) == float(loss_b) and torch.equal(g, g_b)
+    assert float(loss) <= 0
+    np.testing.assert_allclose(float(loss), q.double().sum().item(), rtol=1e-9)
+    gd = g.double()
+    assert abs(float((gd * wd.double()).sum())) <= 1e-4 * float(gd.abs().max() * wd.abs().max()) * 49
+    H, W = w.H, w.W
+    rng = np.random.default_rng(10)
+    wt = np.full(49, 1 / 49, dtype=np.float32)
+    for (y0, x0) in [(0, 0), (H - 24, W - 24), (0, 2000)] + [tuple(rng.integers(10, 4000, 2)) for _ in range(3)]:
+        y1, x1 = y0 + 24, x0 + 24
+        cy0, cy1, cx0, cx1 = max(0, y0 - 3), min(H, y1 + 3), max(0, x0 - 3), min(W, x1 + 3)
+        yy, xx = np.meshgrid(np.arange(cy0, cy1), np.arange(cx0, cx1), indexing="ij")
+        idx = (yy * W + xx).ravel().astype(np.uint64)
+        c1 = w.looks(idx, 0).reshape(3, cy1 - cy0, cx1 - cx0)
+        c2 = w.looks(idx, 1).reshape(3, cy1 - cy0, cx1 - cx0)
+        np.testing.assert_array_equal(s1[:, cy0:cy1, cx0:cx1].cpu().numpy(), c1)
+        _, rq = orc.wishart_fwd(c1, c2, 7, wt, want_map=True)
+        rq = rq.reshape(cy1 - cy0, cx1 - cx0)[y0 - cy0:y1 - cy0, x0 - cx0:x1 - cx0]
+        gq = q[y0:y1, x0:x1].cpu().numpy()
+        assert np.abs(gq - rq).max() <= Q_ABS
