@@ -190,6 +190,29 @@ int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int64_t W, int
                      float* grad_weights, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * wishart_stat_fwd_noalloc -- wishart_stat_fwd for callers that cannot pass a
+ * device workspace: code running inside a host application or framework that
+ * owns every device allocation (so cudaMalloc is unavailable or would fragment
+ * its pool), or a processing loop that must not allocate once it is running.
+ * The paper has no counterpart; this is a property of the library, not of the
+ * method.
+ *
+ * Same arguments and results as wishart_stat_fwd without ws and ws_bytes; the
+ * caller still passes the inputs and outputs.  The per-tile partial sums go to
+ * a fixed 1 MiB device array inside libzinv.so, held by every GPU that loads the
+ * library until the process exits.  Maximum size: ceil(W/64) * ceil(H/8) <=
+ * 131072 tiles (e.g. 8192 x 8192 pixels); larger images return ZINV_ERR_ARG.
+ * The call allocates no device memory.  Its first call on a device looks up the
+ * array's device address for that device; make that first call before any
+ * stream capture.  Every call uses the same array: calls that overlap on the
+ * GPU (other streams, other threads) race and give wrong results.  Nothing in
+ * the array needs to start at zero: each call writes every slot it reads.
+ */
+int wishart_stat_fwd_noalloc(const float* s1, const float* s2, int64_t H, int64_t W,
+                             int64_t plane_ld, int win, const float* weights, float* q_map,
+                             double* d_loss, void* stream);
+
+/*
  * zinv_det_host -- zinv_det over HOST buffers, streamed through the GPU in
  * chunks (the paper's §4.3: data larger than device memory is fed in pieces,
  * processed and pulled back).  Copies in, kernel and copies out of successive

@@ -427,3 +427,73 @@ extern "C" int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int
                                                     d_grad_loss, grad_weights, 0);
   return launch_status();
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of wishart_stat_fwd.  Some callers cannot hand the
+// library a workspace: a plugin inside a host application that owns every
+// device allocation, or a processing loop that must not allocate once it runs.
+// For them the per-tile partial sums live in this fixed device array instead
+// of a caller buffer.  It is part of the module, so every device that loads the
+// library holds these kNoAllocTiles doubles (1 MiB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace zinv {
+namespace {
+constexpr int64_t kNoAllocTiles = 131072;  // one slot per 64 x 8 tile: 8192 x 8192 pixels
+__device__ __align__(256) double g_noalloc_partials[kNoAllocTiles];
+
+struct NoAllocScratch {
+  std::once_flag once;
+  cudaError_t err = cudaErrorNotReady;
+  double* ptr = nullptr;
+};
+NoAllocScratch g_noalloc[kMaxDevices];
+}  // namespace
+}  // namespace zinv
+
+extern "C" int wishart_stat_fwd_noalloc(const float* s1, const float* s2, int64_t H, int64_t W,
+                                        int64_t plane_ld, int win, const float* weights,
+                                        float* q_map, double* d_loss, void* stream) {
+  using namespace zinv;
+  if (H < 1 || W < 1 || H > kMaxLd / W) return ZINV_ERR_ARG;
+  if (win != 3 && win != 5 && win != 7) return ZINV_ERR_ARG;
+  if (plane_ld < H * W || plane_ld > kMaxLd) return ZINV_ERR_ARG;
+  if (!s1 || !s2 || !weights || !d_loss) return ZINV_ERR_ARG;
+  if (!aligned(s1, 8) || !aligned(s2, 8) || !aligned(weights, 4) || !aligned(d_loss, 8) ||
+      !aligned(q_map, 4))
+    return ZINV_ERR_ARG;
+  const int64_t tiles = tile_count(H, W);
+  if (tiles > kNoAllocTiles) return ZINV_ERR_ARG;  // image larger than the fixed scratch
+  DeviceInfo di;
+  int dev = -1;
+  int rc = device_info(&di, &dev);
+  if (rc != ZINV_OK) return rc;
+  // Host code cannot use g_noalloc_partials directly (here it names a host-side
+  // stand-in); take the device address once per device, with that device current.
+  NoAllocScratch& sc = g_noalloc[dev];
+  std::call_once(sc.once, [&]() {
+    sc.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&sc.ptr), g_noalloc_partials);
+    if (sc.err != cudaSuccess) cudaGetLastError();
+  });
+  if (sc.err != cudaSuccess || !sc.ptr) return ZINV_ERR_LAUNCH;
+  if (!device_accessible(s1) || !device_accessible(s2) || !device_accessible(weights) ||
+      !device_accessible(d_loss) || (q_map && !device_accessible(q_map)))
+    return ZINV_ERR_ARG;
+  WsArgs a;
+  a.s[0] = reinterpret_cast<const float2*>(s1);
+  a.s[1] = reinterpret_cast<const float2*>(s2);
+  a.H = H;
+  a.W = W;
+  a.plane_ld = plane_ld;
+  a.weights = weights;
+  a.q_map = q_map;
+  a.partial = sc.ptr;  // every tile writes its own slot before the reduce reads it
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (win) {
+    case 3: rc = launch_tiles(k_wishart_fwd<1>, fwd_smem<1>(), a, st, di); break;
+    case 5: rc = launch_tiles(k_wishart_fwd<2>, fwd_smem<2>(), a, st, di); break;
+    default: rc = launch_tiles(k_wishart_fwd<3>, fwd_smem<3>(), a, st, di); break;
+  }
+  if (rc != ZINV_OK) return rc;
+  k_reduce_tiles<<<1, kRedThreads, 0, st>>>(a.partial, tiles, 1, nullptr, d_loss, 1);
+  return launch_status();
+}
