@@ -8,13 +8,15 @@
 //
 // Boxcar: persistent CTAs walk strip segments (kTW columns x kSeg rows) down
 // the image in steps of kCH output rows.  Per step:
-//   - cp.async brings the next step's kCH raw input rows (plus the r-column
-//     halo, clamp-to-edge) into the other half of a double buffer, so the copy
-//     of step k+1 overlaps the arithmetic of step k;
-//   - phase H: the nine channel products |s0|^2, Re/Im s0 conj s1, Re/Im s0 conj
-//     s2, |s1|^2, Re/Im s1 conj s2, |s2|^2 of each new row and their horizontal
-//     window sums (four adjacent outputs per thread) go into a ring of kRing
-//     rows in shared memory;
+//   - cp.async copies of the step's raw input rows (three planes, the r-column
+//     halo, clamp-to-edge rows; 16-byte copies inside the image, clamped 8-byte
+//     copies on border strips) were issued two steps earlier into a
+//     three-deep ring of raw buffers, so two steps of loads are always in
+//     flight behind the arithmetic;
+//   - phase H: the nine channel products |s0|^2, Re/Im s0 conj s1, Re/Im s0
+//     conj s2, |s1|^2, Re/Im s1 conj s2, |s2|^2 of the 4 + 2r inputs of four
+//     adjacent outputs and their horizontal window sums, into a ring of
+//     kCH + 2r rows (128-bit stores);
 //   - phase V: vertical window sums over the ring (four rows per thread), scale
 //     by 1/N, invert, store (warp-contiguous along x).
 // Each input row is loaded once per strip (plus 2r rows at a segment start and
@@ -139,18 +141,24 @@ __device__ __forceinline__ void stage_products(const MlArgs& a, int64_t ty0, int
 // Boxcar strip walker
 // ---------------------------------------------------------------------------
 constexpr int kSThreads = 128;
-constexpr int kCH = 8;      // output rows per step
-constexpr int kRing = 16;   // ring rows of horizontal sums (>= kCH + 2r)
-constexpr int kSeg = 256;   // rows per strip segment
+constexpr int kCH = 8;       // output rows per step
+constexpr int kSeg = 256;    // rows per strip segment
+constexpr int kStages = 3;   // raw-row buffers in flight
+constexpr int kRawW = kTW + 8;  // raw columns x0-4 .. x0+67 (covers r <= 4), 16-byte aligned
 
 template <int R>
 struct Strip {
-  static constexpr int SW = kTW + 2 * R;                    // input columns per row
-  static constexpr size_t raw_f2 = 2 * 3 * kCH * SW;        // float2 [2][3][kCH][SW]
-  static constexpr size_t ring_f = 9 * kRing * kTW;         // float [9][kRing][kTW]
-  static constexpr size_t smem = raw_f2 * sizeof(float2) + ring_f * sizeof(float);
+  static_assert(R <= 4, "raw rows cover a halo of at most 4");
+  static constexpr int RING = kCH + 2 * R;                      // rows of horizontal sums
+  static constexpr size_t stage_f2 = 3 * kCH * kRawW;           // float2 per raw buffer
+  static constexpr size_t ring_f = 9 * RING * kTW;              // sums [9][RING][kTW]
+  static constexpr size_t smem = kStages * stage_f2 * sizeof(float2) + ring_f * sizeof(float);
 };
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
@@ -163,78 +171,97 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Issues the copies of `rows` input rows starting at relative row rr0 of the
-// segment (absolute row y_begin - R + rr, clamped) into buffer `buf`.
+// Issues the asynchronous copies of `rows` input rows (relative rows rr0 ..,
+// absolute y_begin - R + rr, clamped) of the three planes, columns x0-4 ..
+// x0+67, into raw buffer `buf`: 16-byte copies inside the image, 8-byte copies
+// with clamped columns on strips that touch the left or right border.
 template <int R>
-__device__ __forceinline__ void load_rows(const MlArgs& a, float2* raw, int buf, int64_t y_begin,
-                                          int64_t x0, int rr0, int rows) {
-  using T = Strip<R>;
-  const int n = 3 * rows * T::SW;
-  for (int i = threadIdx.x; i < n; i += kSThreads) {
-    const int p = i / (rows * T::SW);
-    const int rem = i - p * (rows * T::SW);
-    const int r = rem / T::SW, ix = rem - r * T::SW;
+__device__ __forceinline__ void issue_rows(const MlArgs& a, float2* buf, int64_t y_begin,
+                                           int64_t x0, int rr0, int rows, bool vec16) {
+  const int nch = vec16 ? kRawW / 2 : kRawW;  // copies per plane-row
+  const int n = 3 * rows * nch;
+  int pr = threadIdx.x / nch, ch = threadIdx.x - pr * nch;
+  const int dpr = kSThreads / nch, dch = kSThreads - dpr * nch;
+  for (int e = threadIdx.x; e < n; e += kSThreads) {
+    const int p = pr / rows, r = pr - p * rows;
     const int64_t gy = clamp64(y_begin - R + rr0 + r, a.H - 1);
-    const int64_t gx = clamp64(x0 - R + ix, a.W - 1);
-    cp_async8(raw + ((buf * 3 + p) * kCH + r) * T::SW + ix, a.s + p * a.plane_ld + gy * a.W + gx);
+    const float2* row = a.s + p * a.plane_ld + gy * a.W;
+    float2* dst = buf + (p * kCH + r) * kRawW;
+    if (vec16)
+      cp_async16(dst + 2 * ch, row + (x0 - 4) + 2 * ch);
+    else
+      cp_async8(dst + ch, row + clamp64(x0 - 4 + ch, a.W - 1));
+    ch += dch;
+    pr += dpr;
+    if (ch >= nch) {
+      ch -= nch;
+      ++pr;
+    }
   }
 }
 
 template <int R, int ALG, bool STAT>
 __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
   using T = Strip<R>;
-  constexpr int SW = T::SW;
   extern __shared__ __align__(16) float smem[];
   float2* raw = reinterpret_cast<float2*>(smem);
-  float* ring = smem + 2 * T::raw_f2;
+  float* ring = smem + 2 * kStages * T::stage_f2;
   const int64_t strips_x = (a.W + kTW - 1) / kTW;
   const int64_t segs = (a.H + kSeg - 1) / kSeg;
   const int64_t units = strips_x * segs;
   const float invN = 1.0f / (float)((2 * R + 1) * (2 * R + 1));
+  const bool aligned16 = ((a.W & 1) == 0) && ((a.plane_ld & 1) == 0) &&
+                         ((reinterpret_cast<uintptr_t>(a.s) & 15) == 0);
   uint32_t c0 = 0, c1 = 0;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t x0 = (u % strips_x) * kTW;
     const int64_t y_begin = (u / strips_x) * kSeg;
     const int64_t y_end = (y_begin + kSeg < a.H) ? y_begin + kSeg : a.H;
     const int out_rows = (int)(y_end - y_begin);
-    // job 0: the 2R rows above the first output row's window centre; job j >= 1:
-    // input rows 2R + (j-1) kCH .. + kCH (relative), output rows (j-1) kCH .. + kCH.
+    const bool vec16 = aligned16 && x0 >= 4 && x0 + kTW + 4 <= a.W;
+    // job 0: input rows 0 .. 2R-1 (relative to y_begin - R), no output;
+    // job j >= 1: input rows 2R + (j-1) kCH .. + kCH, output rows (j-1) kCH .. + kCH.
     const int jobs = 1 + (out_rows + kCH - 1) / kCH;
-    __syncthreads();  // the previous unit is done with raw and ring
-    load_rows<R>(a, raw, 0, y_begin, x0, 0, 2 * R);
-    cp_async_commit();
+    __syncthreads();  // the previous unit is done with the raw buffers and the ring
+    for (int j = 0; j < kStages - 1; ++j) {
+      if (j < jobs)
+        issue_rows<R>(a, raw + j * T::stage_f2, y_begin, x0, j == 0 ? 0 : 2 * R + (j - 1) * kCH,
+                      j == 0 ? 2 * R : kCH, vec16);
+      cp_async_commit();
+    }
     for (int j = 0; j < jobs; ++j) {
+      const int jn = j + kStages - 1;  // the job whose copies start now
+      if (jn < jobs)
+        issue_rows<R>(a, raw + (jn % kStages) * T::stage_f2, y_begin, x0, 2 * R + (jn - 1) * kCH,
+                      kCH, vec16);
+      cp_async_commit();
+      cp_async_wait<kStages - 1>();  // this thread's copies of job j have landed
+      __syncthreads();               // everyone's have
       const int rr0 = j == 0 ? 0 : 2 * R + (j - 1) * kCH;
       const int rows = j == 0 ? 2 * R : kCH;
-      if (j + 1 < jobs) {
-        load_rows<R>(a, raw, (j + 1) & 1, y_begin, x0, 2 * R + j * kCH, kCH);
-        cp_async_commit();
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncthreads();
-      // phase H: products and horizontal sums of the job's rows -> ring
-      const float2* rb = raw + (size_t)((j & 1) * 3) * kCH * SW;
+      const float2* rb = raw + (j % kStages) * T::stage_f2;
+      // phase H: products of 4 + 2R pixels and horizontal sums of four adjacent
+      // outputs per work item, rows of this job -> ring
       for (int i = threadIdx.x; i < rows * (kTW / 4); i += kSThreads) {
-        const int r = i % rows, xr = (i / rows) * 4;
+        const int r = i / (kTW / 4), xr = (i % (kTW / 4)) * 4;
+        const int cbase = xr + 4 - R;  // raw column of the run's first input
         float pv[9][4 + 2 * R];
 #pragma unroll
         for (int k = 0; k < 4 + 2 * R; ++k) {
-          const float2 s0 = rb[(0 * kCH + r) * SW + xr + k];
-          const float2 s1 = rb[(1 * kCH + r) * SW + xr + k];
-          const float2 s2 = rb[(2 * kCH + r) * SW + xr + k];
-          float p[9];
-          channels(s0, s1, s2, p);
+          const float2 s0 = rb[(0 * kCH + r) * kRawW + cbase + k];
+          const float2 s1 = rb[(1 * kCH + r) * kRawW + cbase + k];
+          const float2 s2 = rb[(2 * kCH + r) * kRawW + cbase + k];
+          float pp[9];
+          channels(s0, s1, s2, pp);
 #pragma unroll
-          for (int c = 0; c < 9; ++c) pv[c][k] = p[c];
+          for (int c = 0; c < 9; ++c) pv[c][k] = pp[c];
         }
-        const int slot = (rr0 + r) % kRing;
+        const int slot = (rr0 + r) % T::RING;
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
           float o[4];
           window4<R>(pv[c], o);
-          *reinterpret_cast<float4*>(ring + (c * kRing + slot) * kTW + xr) =
+          *reinterpret_cast<float4*>(ring + (c * T::RING + slot) * kTW + xr) =
               make_float4(o[0], o[1], o[2], o[3]);
         }
       }
@@ -245,15 +272,17 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
       const int orows = (out_rows - oy0) < kCH ? (out_rows - oy0) : kCH;
       for (int i = threadIdx.x; i < kTW * ((orows + 3) / 4); i += kSThreads) {
         const int x = i % kTW, yq = (i / kTW) * 4;
+        int off[4 + 2 * R];  // ring offsets of the rows this item reads
+#pragma unroll
+        for (int k = 0; k < 4 + 2 * R; ++k) off[k] = ((oy0 + yq + k) % T::RING) * kTW + x;
         float z[4][9];
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
-          float v[4 + 2 * R];
+          float w[4 + 2 * R];
 #pragma unroll
-          for (int k = 0; k < 4 + 2 * R; ++k)
-            v[k] = ring[(c * kRing + (oy0 + yq + k) % kRing) * kTW + x];
+          for (int k = 0; k < 4 + 2 * R; ++k) w[k] = ring[c * T::RING * kTW + off[k]];
           float o[4];
-          window4<R>(v, o);
+          window4<R>(w, o);
 #pragma unroll
           for (int q = 0; q < 4; ++q) z[q][c] = o[q] * invN;
         }
@@ -266,6 +295,7 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
       }
     }
   }
+  cp_async_wait<0>();
   if (STAT && a.counts) add_counts(a.counts, c0, c1);
 }
 

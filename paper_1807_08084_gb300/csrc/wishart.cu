@@ -14,9 +14,10 @@
 // route of Algorithm 2 (Dot2), so the log-dets keep FP32 accuracy.
 //
 // Tiles of 64 x 8 outputs, 128 threads, each thread four adjacent outputs of one
-// row.  Both dates' channel products for the tile and its halo sit in shared
-// memory; a thread slides over them with 128-bit loads, 28 FMAs per loaded row
-// and channel.  Each tile writes its partial sums (FP64) to the workspace; a
+// row.  One date's channel products for the tile and its halo sit in shared
+// memory at a time, staged from values each thread prefetched into registers
+// while the previous stage was being used; a thread slides over a product row
+// with 128-bit loads, 28 FMAs per loaded row, one channel at a time.  Each tile writes its partial sums (FP64) to the workspace; a
 // one-block-per-output kernel adds them in tile order.  No float atomics: the
 // results are the same bits on every run.
 #include "common.cuh"
@@ -44,8 +45,10 @@ struct WTile {
   static constexpr int SH = kTH + 2 * R;
   static constexpr int SW = kTW + 2 * R;
   static constexpr int SWP = (SW + 3) / 4 * 4;
-  static constexpr int NV = (4 + 2 * R + 3) / 4;  // float4 loads per row segment
-  static constexpr int P_FLOATS = 2 * 9 * SH * SWP;
+  static constexpr int NV = (4 + 2 * R + 3) / 4;              // float4 loads per row segment
+  static constexpr int KO = (SH * SW + kWT - 1) / kWT;       // staged pixels per thread
+  static constexpr int P_FLOATS = 9 * SH * SWP;              // one date's products
+  static constexpr int Z_FLOATS = 2 * 9 * kTH * kTW;         // Z (then G) of both dates
 };
 
 __device__ __forceinline__ int64_t clampi(int64_t v, int64_t hi) {
@@ -64,46 +67,61 @@ __device__ __forceinline__ void products(float2 s0, float2 s1, float2 s2, float 
   p[8] = s2.x * s2.x + s2.y * s2.y;
 }
 
-// Stages both dates' channel products of the tile and its halo into
-// P[t][c][SH][SWP]; all of a thread's loads for one date are in flight together.
+// Loads into registers the three components of the staged pixels this thread
+// owns (pixel i = tid + k*kWT of the tile plus halo, row-major, clamp-to-edge).
 template <int R>
-__device__ __forceinline__ void stage(const WsArgs& a, int64_t ty0, int64_t tx0, float* P) {
+__device__ __forceinline__ void prefetch(const WsArgs& a, int t, int64_t tile,
+                                         float2 (&v)[WTile<R>::KO][3]) {
   using T = WTile<R>;
-  constexpr int N = T::SH * T::SW;
-  constexpr int KMAX = (N + kWT - 1) / kWT;
+  const int64_t tiles_x = (a.W + kTW - 1) / kTW;
+  const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
+  int r = threadIdx.x / T::SW, x = threadIdx.x - r * T::SW;
+  constexpr int dr = kWT / T::SW, dx = kWT - dr * T::SW;
 #pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    float2 v[KMAX][3];
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-      const int i = threadIdx.x + k * kWT;
-      if (i < N) {
-        const int iy = i / T::SW, ix = i - (i / T::SW) * T::SW;
-        const int64_t q = clampi(ty0 - R + iy, a.H - 1) * a.W + clampi(tx0 - R + ix, a.W - 1);
-        v[k][0] = __ldg(a.s[t] + q);
-        v[k][1] = __ldg(a.s[t] + a.plane_ld + q);
-        v[k][2] = __ldg(a.s[t] + 2 * a.plane_ld + q);
-      }
+  for (int k = 0; k < T::KO; ++k) {
+    if (r < T::SH) {
+      const int64_t q = clampi(ty0 - R + r, a.H - 1) * a.W + clampi(tx0 - R + x, a.W - 1);
+      v[k][0] = __ldg(a.s[t] + q);
+      v[k][1] = __ldg(a.s[t] + a.plane_ld + q);
+      v[k][2] = __ldg(a.s[t] + 2 * a.plane_ld + q);
     }
+    x += dx;
+    r += dr;
+    if (x >= T::SW) {
+      x -= T::SW;
+      ++r;
+    }
+  }
+}
+
+// The nine channel products of the prefetched pixels -> P[c][SH][SWP].
+template <int R>
+__device__ __forceinline__ void store_products(const float2 (&v)[WTile<R>::KO][3], float* P) {
+  using T = WTile<R>;
+  int r = threadIdx.x / T::SW, x = threadIdx.x - r * T::SW;
+  constexpr int dr = kWT / T::SW, dx = kWT - dr * T::SW;
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-      const int i = threadIdx.x + k * kWT;
-      if (i < N) {
-        const int iy = i / T::SW, ix = i - (i / T::SW) * T::SW;
-        float p[9];
-        products(v[k][0], v[k][1], v[k][2], p);
+  for (int k = 0; k < T::KO; ++k) {
+    if (r < T::SH) {
+      float p[9];
+      products(v[k][0], v[k][1], v[k][2], p);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) P[((t * 9 + c) * T::SH + iy) * T::SWP + ix] = p[c];
-      }
+      for (int c = 0; c < 9; ++c) P[(c * T::SH + r) * T::SWP + x] = p[c];
+    }
+    x += dx;
+    r += dr;
+    if (x >= T::SW) {
+      x -= T::SW;
+      ++r;
     }
   }
 }
 
 template <int R>
-__device__ __forceinline__ void load_row(const float* P, int t, int c, int iy, int x0,
+__device__ __forceinline__ void load_row(const float* P, int c, int iy, int x0,
                                          float row[4 * WTile<R>::NV]) {
   using T = WTile<R>;
-  const float4* src = reinterpret_cast<const float4*>(P + ((t * 9 + c) * T::SH + iy) * T::SWP + x0);
+  const float4* src = reinterpret_cast<const float4*>(P + (c * T::SH + iy) * T::SWP + x0);
 #pragma unroll
   for (int q = 0; q < T::NV; ++q) {
     const float4 v = src[q];
@@ -114,34 +132,28 @@ __device__ __forceinline__ void load_row(const float* P, int t, int c, int iy, i
   }
 }
 
-// Z_t for the thread's four outputs (row y, columns x0..x0+3 of the tile).
+// Z_t of the thread's four outputs (tile row y, columns x0..x0+3), one channel
+// at a time (a runtime loop: small code), into Zb[t][c][y][x0..x0+3].
 template <int R>
-__device__ __forceinline__ void window_cov(const float* P, const float* wsh, int y, int x0,
-                                           float z[2][4][9]) {
+__device__ __forceinline__ void window_cov(const float* P, const float* wsh, int t, int y,
+                                           int x0, float* Zb) {
   constexpr int L = 2 * R + 1;
+#pragma unroll 1
+  for (int c = 0; c < 9; ++c) {
+    float z[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int t = 0; t < 2; ++t)
+    for (int dy = 0; dy < L; ++dy) {
+      float row[4 * WTile<R>::NV];
+      load_row<R>(P, c, y + dy, x0, row);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int dx = 0; dx < L; ++dx) {
+        const float wk = wsh[dy * L + dx];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) z[t][i][c] = 0.0f;
-#pragma unroll
-  for (int dy = 0; dy < L; ++dy) {
-    float wr[L];
-#pragma unroll
-    for (int dx = 0; dx < L; ++dx) wr[dx] = wsh[dy * L + dx];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        float row[4 * WTile<R>::NV];
-        load_row<R>(P, t, c, y + dy, x0, row);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int dx = 0; dx < L; ++dx) z[t][i][c] = fmaf(wr[dx], row[i + dx], z[t][i][c]);
+        for (int i = 0; i < 4; ++i) z[i] = fmaf(wk, row[i + dx], z[i]);
       }
     }
+    *reinterpret_cast<float4*>(Zb + ((t * 9 + c) * kTH + y) * kTW + x0) =
+        make_float4(z[0], z[1], z[2], z[3]);
   }
 }
 
@@ -165,36 +177,50 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kWT) k_wishart_fwd(WsArgs a) {
+__global__ void __launch_bounds__(kWT, 3) k_wishart_fwd(WsArgs a) {
   using T = WTile<R>;
   constexpr int L = 2 * R + 1;
   extern __shared__ __align__(16) float smem[];
   float* P = smem;
-  float* wsh = smem + T::P_FLOATS;
+  float* Zb = smem + T::P_FLOATS;
+  float* wsh = Zb + T::Z_FLOATS;
   double* red = reinterpret_cast<double*>(wsh + 64);
   for (int i = threadIdx.x; i < L * L; i += blockDim.x) wsh[i] = a.weights[i];
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
   const int y = threadIdx.x / (kTW / 4), x0 = (threadIdx.x % (kTW / 4)) * 4;
   const float six_ln2 = 4.15888308335967185650f;
+  float2 v[T::KO][3];
+  if ((int64_t)blockIdx.x < tiles) prefetch<R>(a, 0, blockIdx.x, v);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
-    __syncthreads();  // previous tile's readers are done with P
-    stage<R>(a, ty0, tx0, P);
-    __syncthreads();
-    float z[2][4][9];
-    window_cov<R>(P, wsh, y, x0, z);
+#pragma unroll 1
+    for (int t = 0; t < 2; ++t) {
+      __syncthreads();  // everyone is done reading P
+      store_products<R>(v, P);
+      if (t == 0)
+        prefetch<R>(a, 1, tile, v);
+      else if (tile + gridDim.x < tiles)
+        prefetch<R>(a, 0, tile + gridDim.x, v);
+      __syncthreads();
+      window_cov<R>(P, wsh, t, y, x0, Zb);
+    }
+    // per output: compensated log-dets of Z1, Z2 and Z1 + Z2 (own Zb entries only)
     double qsum = 0.0;
     const int64_t gy = ty0 + y;
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < 4; ++i) {
       const int64_t gx = tx0 + x0 + i;
       if (gy >= a.H || gx >= a.W) continue;
-      float z12[9];
+      float z1[9], z2[9], z12[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) z12[c] = z[0][i][c] + z[1][i][c];
-      const float l1 = log_dd(det_comp<float>(z[0][i]));
-      const float l2 = log_dd(det_comp<float>(z[1][i]));
+      for (int c = 0; c < 9; ++c) {
+        z1[c] = Zb[((0 * 9 + c) * kTH + y) * kTW + x0 + i];
+        z2[c] = Zb[((1 * 9 + c) * kTH + y) * kTW + x0 + i];
+        z12[c] = z1[c] + z2[c];
+      }
+      const float l1 = log_dd(det_comp<float>(z1));
+      const float l2 = log_dd(det_comp<float>(z2));
       const float l12 = log_dd(det_comp<float>(z12));
       const float q = (l1 + l2) - 2.0f * l12 + six_ln2;
       if (a.q_map) a.q_map[gy * a.W + gx] = q;
@@ -206,38 +232,39 @@ __global__ void __launch_bounds__(kWT) k_wishart_fwd(WsArgs a) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kWT) k_wishart_bwd(WsArgs a) {
+__global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
   using T = WTile<R>;
   constexpr int L = 2 * R + 1;
   constexpr int K = L * L;
   extern __shared__ __align__(16) float smem[];
   float* P = smem;
-  float* G = smem + T::P_FLOATS;          // [2][9][kTH][kTW]
-  float* wsh = G + 2 * 9 * kTH * kTW;
+  float* G = smem + T::P_FLOATS;  // [2][9][kTH][kTW]: Z_t, then the packed M_t
+  float* wsh = G + T::Z_FLOATS;
   double* red = reinterpret_cast<double*>(wsh + 64);  // [4 warps][K]
   for (int i = threadIdx.x; i < K; i += blockDim.x) wsh[i] = a.weights[i];
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
   const int y = threadIdx.x / (kTW / 4), x0 = (threadIdx.x % (kTW / 4)) * 4;
+  float2 v[T::KO][3];
+  // P holds one date at a time.  Per tile: stage date 0 (Z_0), stage date 1
+  // (Z_1, then its correlation while still staged), stage date 0 again (its
+  // correlation).  Each stage's loads were issued during the previous stage.
+  if ((int64_t)blockIdx.x < tiles) prefetch<R>(a, 0, blockIdx.x, v);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
-    __syncthreads();
-    stage<R>(a, ty0, tx0, P);
-    __syncthreads();
-    {
-      // Z_t of the thread's four outputs, parked in G's slots (G[t][c][y][x0+i])
-      float z[2][4][9];
-      window_cov<R>(P, wsh, y, x0, z);
-#pragma unroll
-      for (int t = 0; t < 2; ++t)
-#pragma unroll
-        for (int c = 0; c < 9; ++c)
-          *reinterpret_cast<float4*>(G + ((t * 9 + c) * kTH + y) * kTW + x0) =
-              make_float4(z[t][0][c], z[t][1][c], z[t][2][c], z[t][3][c]);
+    // Z_0 and Z_1
+#pragma unroll 1
+    for (int t = 0; t < 2; ++t) {
+      __syncthreads();
+      store_products<R>(v, P);
+      if (t == 0) prefetch<R>(a, 1, tile, v);
+      else prefetch<R>(a, 0, tile, v);  // date 0 again, for its correlation
+      __syncthreads();
+      window_cov<R>(P, wsh, t, y, x0, G);
     }
+    // per output: three compensated inverses, M_t = W_t - 2 W_12 in packed
+    // gradient form written over the thread's own Z slots
     {
-      // per output: the three compensated inverses, then M_t in packed gradient
-      // form, written over the same slots (a thread only touches its own)
       const int64_t gy = ty0 + y;
 #pragma unroll 1
       for (int i = 0; i < 4; ++i) {
@@ -262,20 +289,28 @@ __global__ void __launch_bounds__(kWT) k_wishart_bwd(WsArgs a) {
         }
       }
     }
-    // dL/dw_k over this thread's four pixels: sum_t sum_c G_t[c](p) P_t[c](p + k)
+    // dL/dw_k over this thread's four pixels: sum_t sum_c G_t[c](p) P_t[c](p + k);
+    // P still holds date 1: correlate it first, then stage date 0.
     float acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-#pragma unroll
+#pragma unroll 1
+    for (int step = 0; step < 2; ++step) {
+      const int t = 1 - step;
+      if (step == 1) {
+        __syncthreads();
+        store_products<R>(v, P);
+        if (tile + gridDim.x < tiles) prefetch<R>(a, 0, tile + gridDim.x, v);
+        __syncthreads();
+      }
+#pragma unroll 1
       for (int c = 0; c < 9; ++c) {
         const float4 gv = *reinterpret_cast<const float4*>(G + ((t * 9 + c) * kTH + y) * kTW + x0);
         const float gi[4] = {gv.x, gv.y, gv.z, gv.w};
 #pragma unroll
         for (int dy = 0; dy < L; ++dy) {
           float row[4 * WTile<R>::NV];
-          load_row<R>(P, t, c, y + dy, x0, row);
+          load_row<R>(P, c, y + dy, x0, row);
 #pragma unroll
           for (int dx = 0; dx < L; ++dx)
 #pragma unroll
@@ -287,16 +322,16 @@ __global__ void __launch_bounds__(kWT) k_wishart_bwd(WsArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double v = (double)acc[k];
+      double vsum = (double)acc[k];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp * K + k] = v;
+      for (int o = 16; o > 0; o >>= 1) vsum += __shfl_down_sync(0xffffffffu, vsum, o);
+      if (lane == 0) red[warp * K + k] = vsum;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w * K + k];
-      a.partial[tile * K + k] = s;
+      double ssum = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) ssum += red[w * K + k];
+      a.partial[tile * K + k] = ssum;
     }
   }
 }
@@ -322,11 +357,13 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 template <int R>
-size_t fwd_smem() { return (WTile<R>::P_FLOATS + 64) * sizeof(float) + 8 * sizeof(double); }
+size_t fwd_smem() {
+  return (WTile<R>::P_FLOATS + WTile<R>::Z_FLOATS + 64) * sizeof(float) + 8 * sizeof(double);
+}
 template <int R>
 size_t bwd_smem() {
   constexpr int K = (2 * R + 1) * (2 * R + 1);
-  return (WTile<R>::P_FLOATS + 2 * 9 * kTH * kTW + 64) * sizeof(float) + 4 * K * sizeof(double);
+  return (WTile<R>::P_FLOATS + WTile<R>::Z_FLOATS + 64) * sizeof(float) + 4 * K * sizeof(double);
 }
 
 int64_t tile_count(int64_t H, int64_t W) {
