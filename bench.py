@@ -152,18 +152,13 @@ def dist_setup(args):
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_1807_08084_gb300 import shard
+    shard.barrier()
 
 
 def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1807_08084_gb300 import shard
+    return shard.max_over_ranks(x, device="cuda")
 
 
 def timed(fn, steps: int, warmup: int, world: int) -> float:
@@ -269,7 +264,8 @@ def main():
         w = S.scaled(w, args.rows, w.W)
     if world > 1:
         from dataclasses import replace
-        w = replace(w, seed=w.seed + 1000 * rank)
+        from paper_1807_08084_gb300 import shard
+        w = replace(w, seed=shard.rank_seed(w.seed, rank))
     n = w.n
     z = G.packed_z(w)
     zinv = torch.empty_like(z)

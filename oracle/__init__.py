@@ -85,6 +85,9 @@ class Oracle:
         lib.oracle_wishart_fwd.argtypes = [_D, _D, _I64, _I64, _I64, ctypes.c_int, _D, _D, _D]
         lib.oracle_wishart_bwd.argtypes = [_D, _D, _I64, _I64, _I64, ctypes.c_int, _D,
                                            ctypes.c_double, _D]
+        lib.oracle_wishart_bwd_rows.argtypes = [_D, _D, _I64, _I64, _I64, ctypes.c_int, _D,
+                                                ctypes.c_double, _I64, _I64, _D]
+        lib.oracle_wishart_bwd_rows.restype = None
         for f in ("oracle_zinv_det", "oracle_det_expansions", "oracle_inverse_full",
                   "oracle_eigvals", "oracle_multilook", "oracle_zinv_det_bwd",
                   "oracle_wishart_fwd", "oracle_wishart_bwd"):
@@ -168,13 +171,18 @@ class Oracle:
                                     _ptr(q), _ptr(loss))
         return (float(loss[0]), q) if want_map else float(loss[0])
 
-    def wishart_bwd(self, s1, s2, win: int, weights, g: float = 1.0) -> np.ndarray:
+    def wishart_bwd(self, s1, s2, win: int, weights, g: float = 1.0, rows=None) -> np.ndarray:
+        """g dL/dw; rows=(y_lo, y_hi) sums over those output rows only."""
         b1, H, W = _slc_f64(s1)
         b2, _, _ = _slc_f64(s2)
         w = _f64(weights).reshape(-1)
         out = np.empty(win * win)
-        self.lib.oracle_wishart_bwd(_ptr(b1), _ptr(b2), H, W, H * W, int(win), _ptr(w),
-                                    float(g), _ptr(out))
+        if rows is None:
+            self.lib.oracle_wishart_bwd(_ptr(b1), _ptr(b2), H, W, H * W, int(win), _ptr(w),
+                                        float(g), _ptr(out))
+        else:
+            self.lib.oracle_wishart_bwd_rows(_ptr(b1), _ptr(b2), H, W, H * W, int(win), _ptr(w),
+                                             float(g), int(rows[0]), int(rows[1]), _ptr(out))
         return out
 
 

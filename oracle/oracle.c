@@ -618,14 +618,15 @@ void oracle_wishart_fwd(const double* s1, const double* s2, int64_t H, int64_t W
  * dq = tr(M1 dZ1) + tr(M2 dZ2), M_t = W_t - 2 W_12, and dZ_t(p)/dw_k =
  * S S^H with S = s_t(clamp(p + offset_k)), so dL/dw_k = sum_p sum_t S^H M_t(p) S.
  */
-void oracle_wishart_bwd(const double* s1, const double* s2, int64_t H, int64_t W,
-                        int64_t plane_ld, int win, const double* w, double g, double* grad_w)
+void oracle_wishart_bwd_rows(const double* s1, const double* s2, int64_t H, int64_t W,
+                             int64_t plane_ld, int win, const double* w, double g, int64_t y_lo,
+                             int64_t y_hi, double* grad_w)
 {
     int r = (win - 1) / 2;
     int K = win * win;
     for (int k = 0; k < K; ++k) grad_w[k] = 0.0;
     const double* s_t[2] = {s1, s2};
-    for (int64_t y = 0; y < H; ++y)
+    for (int64_t y = y_lo; y < y_hi; ++y)
         for (int64_t x = 0; x < W; ++x) {
             mat3 Z[2], Wt[2], Z12, W12;
             Z[0] = window_cov(s1, H, W, plane_ld, win, w, y, x);
@@ -660,4 +661,10 @@ void oracle_wishart_bwd(const double* s1, const double* s2, int64_t H, int64_t W
                     }
             }
         }
+}
+
+void oracle_wishart_bwd(const double* s1, const double* s2, int64_t H, int64_t W,
+                        int64_t plane_ld, int win, const double* w, double g, double* grad_w)
+{
+    oracle_wishart_bwd_rows(s1, s2, H, W, plane_ld, win, w, g, 0, H, grad_w);
 }

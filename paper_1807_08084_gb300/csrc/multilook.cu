@@ -63,8 +63,33 @@ __device__ __forceinline__ void channels(float2 s0, float2 s1, float2 s2, float 
   p[8] = s2.x * s2.x + s2.y * s2.y;
 }
 
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 // Sums of L = 2R+1 consecutive values for four adjacent outputs:
 // out[j] = v[j] + ... + v[j+L-1], j = 0..3, sharing the common middle.
+// float2 sums two channels at once with Blackwell's packed FP32 adds.
+template <int R, typename V>
+__device__ __forceinline__ void window4v(const V* v, V out[4]) {
+  constexpr int L = 2 * R + 1;
+  if constexpr (L == 3) {
+    const V a = vadd(v[1], v[2]), b = vadd(v[3], v[4]);
+    out[0] = vadd(v[0], a);
+    out[1] = vadd(a, v[3]);
+    out[2] = vadd(v[2], b);
+    out[3] = vadd(b, v[5]);
+  } else {
+    V core = v[3];
+#pragma unroll
+    for (int k = 4; k < L; ++k) core = vadd(core, v[k]);
+    const V a = vadd(v[1], v[2]), b = vadd(v[L], v[L + 1]);
+    out[0] = vadd(core, vadd(v[0], a));
+    out[1] = vadd(core, vadd(a, v[L]));
+    out[2] = vadd(core, vadd(v[2], b));
+    out[3] = vadd(core, vadd(b, v[L + 2]));
+  }
+}
+
 template <int R>
 __device__ __forceinline__ void window4(const float* v, float out[4]) {
   constexpr int L = 2 * R + 1;
@@ -151,7 +176,8 @@ struct Strip {
   static_assert(R <= 4, "raw rows cover a halo of at most 4");
   static constexpr int RING = kCH + 2 * R;                      // rows of horizontal sums
   static constexpr size_t stage_f2 = 3 * kCH * kRawW;           // float2 per raw buffer
-  static constexpr size_t ring_f = 9 * RING * kTW;              // sums [9][RING][kTW]
+  // horizontal sums: float2 [4][RING][kTW] (channel pairs) then float [RING][kTW]
+  static constexpr size_t ring_f = 9 * RING * kTW;
   static constexpr size_t smem = kStages * stage_f2 * sizeof(float2) + ring_f * sizeof(float);
 };
 
@@ -175,28 +201,34 @@ __device__ __forceinline__ void cp_async_wait() {
 // absolute y_begin - R + rr, clamped) of the three planes, columns x0-4 ..
 // x0+67, into raw buffer `buf`: 16-byte copies inside the image, 8-byte copies
 // with clamped columns on strips that touch the left or right border.
-template <int R>
-__device__ __forceinline__ void issue_rows(const MlArgs& a, float2* buf, int64_t y_begin,
-                                           int64_t x0, int rr0, int rows, bool vec16) {
-  const int nch = vec16 ? kRawW / 2 : kRawW;  // copies per plane-row
-  const int n = 3 * rows * nch;
-  int pr = threadIdx.x / nch, ch = threadIdx.x - pr * nch;
-  const int dpr = kSThreads / nch, dch = kSThreads - dpr * nch;
+template <int R, int ROWS, bool VEC16>
+__device__ __forceinline__ void issue_rows_t(const MlArgs& a, float2* buf, int64_t y_begin,
+                                             int64_t x0, int rr0) {
+  constexpr int nch = VEC16 ? kRawW / 2 : kRawW;  // copies per plane-row
+  constexpr int n = 3 * ROWS * nch;
+#pragma unroll 2
   for (int e = threadIdx.x; e < n; e += kSThreads) {
-    const int p = pr / rows, r = pr - p * rows;
+    const int pr = e / nch, ch = e - (e / nch) * nch;
+    const int p = pr / ROWS, r = pr - p * ROWS;
     const int64_t gy = clamp64(y_begin - R + rr0 + r, a.H - 1);
     const float2* row = a.s + p * a.plane_ld + gy * a.W;
     float2* dst = buf + (p * kCH + r) * kRawW;
-    if (vec16)
+    if (VEC16)
       cp_async16(dst + 2 * ch, row + (x0 - 4) + 2 * ch);
     else
       cp_async8(dst + ch, row + clamp64(x0 - 4 + ch, a.W - 1));
-    ch += dch;
-    pr += dpr;
-    if (ch >= nch) {
-      ch -= nch;
-      ++pr;
-    }
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void issue_rows(const MlArgs& a, float2* buf, int64_t y_begin,
+                                           int64_t x0, int rr0, int rows, bool vec16) {
+  if (rows == kCH) {
+    if (vec16) issue_rows_t<R, kCH, true>(a, buf, y_begin, x0, rr0);
+    else issue_rows_t<R, kCH, false>(a, buf, y_begin, x0, rr0);
+  } else {
+    if (vec16) issue_rows_t<R, 2 * R, true>(a, buf, y_begin, x0, rr0);
+    else issue_rows_t<R, 2 * R, false>(a, buf, y_begin, x0, rr0);
   }
 }
 
@@ -205,7 +237,8 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
   using T = Strip<R>;
   extern __shared__ __align__(16) float smem[];
   float2* raw = reinterpret_cast<float2*>(smem);
-  float* ring = smem + 2 * kStages * T::stage_f2;
+  float2* ring2 = reinterpret_cast<float2*>(smem + 2 * kStages * T::stage_f2);
+  float* ring1 = smem + 2 * kStages * T::stage_f2 + 8 * T::RING * kTW;
   const int64_t strips_x = (a.W + kTW - 1) / kTW;
   const int64_t segs = (a.H + kSeg - 1) / kSeg;
   const int64_t units = strips_x * segs;
@@ -245,7 +278,8 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
       for (int i = threadIdx.x; i < rows * (kTW / 4); i += kSThreads) {
         const int r = i / (kTW / 4), xr = (i % (kTW / 4)) * 4;
         const int cbase = xr + 4 - R;  // raw column of the run's first input
-        float pv[9][4 + 2 * R];
+        float2 pv2[4][4 + 2 * R];
+        float pv8[4 + 2 * R];
 #pragma unroll
         for (int k = 0; k < 4 + 2 * R; ++k) {
           const float2 s0 = rb[(0 * kCH + r) * kRawW + cbase + k];
@@ -253,17 +287,24 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
           const float2 s2 = rb[(2 * kCH + r) * kRawW + cbase + k];
           float pp[9];
           channels(s0, s1, s2, pp);
-#pragma unroll
-          for (int c = 0; c < 9; ++c) pv[c][k] = pp[c];
+          pv2[0][k] = make_float2(pp[0], pp[5]);
+          pv2[1][k] = make_float2(pp[1], pp[2]);
+          pv2[2][k] = make_float2(pp[3], pp[4]);
+          pv2[3][k] = make_float2(pp[6], pp[7]);
+          pv8[k] = pp[8];
         }
         const int slot = (rr0 + r) % T::RING;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-          float o[4];
-          window4<R>(pv[c], o);
-          *reinterpret_cast<float4*>(ring + (c * T::RING + slot) * kTW + xr) =
-              make_float4(o[0], o[1], o[2], o[3]);
+        for (int q = 0; q < 4; ++q) {
+          float2 o[4];
+          window4v<R>(pv2[q], o);
+          float4* dst = reinterpret_cast<float4*>(ring2 + (q * T::RING + slot) * kTW + xr);
+          dst[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+          dst[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
         }
+        float o8[4];
+        window4v<R>(pv8, o8);
+        *reinterpret_cast<float4*>(ring1 + slot * kTW + xr) = make_float4(o8[0], o8[1], o8[2], o8[3]);
       }
       __syncthreads();
       if (j == 0) continue;
@@ -273,18 +314,39 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
       for (int i = threadIdx.x; i < kTW * ((orows + 3) / 4); i += kSThreads) {
         const int x = i % kTW, yq = (i / kTW) * 4;
         int off[4 + 2 * R];  // ring offsets of the rows this item reads
+        {
+          int slot = (oy0 + yq) % T::RING;
 #pragma unroll
-        for (int k = 0; k < 4 + 2 * R; ++k) off[k] = ((oy0 + yq + k) % T::RING) * kTW + x;
+          for (int k = 0; k < 4 + 2 * R; ++k) {
+            off[k] = slot * kTW + x;
+            slot = (slot + 1 == T::RING) ? 0 : slot + 1;
+          }
+        }
         float z[4][9];
+        const float2 inv2 = make_float2(invN, invN);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
+        for (int q = 0; q < 4; ++q) {
+          float2 w[4 + 2 * R];
+#pragma unroll
+          for (int k = 0; k < 4 + 2 * R; ++k) w[k] = ring2[q * T::RING * kTW + off[k]];
+          float2 o[4];
+          window4v<R>(w, o);
+          constexpr int lo[4] = {0, 1, 3, 6}, hi[4] = {5, 2, 4, 7};
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const float2 zz = __fmul2_rn(o[m], inv2);
+            z[m][lo[q]] = zz.x;
+            z[m][hi[q]] = zz.y;
+          }
+        }
+        {
           float w[4 + 2 * R];
 #pragma unroll
-          for (int k = 0; k < 4 + 2 * R; ++k) w[k] = ring[c * T::RING * kTW + off[k]];
+          for (int k = 0; k < 4 + 2 * R; ++k) w[k] = ring1[off[k]];
           float o[4];
-          window4<R>(w, o);
+          window4v<R>(w, o);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) z[q][c] = o[q] * invN;
+          for (int m = 0; m < 4; ++m) z[m][8] = o[m] * invN;
         }
         const int64_t gx = x0 + x;
 #pragma unroll

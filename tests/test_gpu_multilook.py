@@ -96,14 +96,18 @@ def test_weighted_window(zlib, orc, win):
     check(zinv, det, reference(orc, s_np, win, wts), "plain_fp64")
 
 
-def test_weighted_equals_boxcar(zlib):
-    """The weighted path with w = 1/N is the boxcar up to summation order."""
+def test_weighted_equals_boxcar(zlib, orc):
+    """The weighted path with w = 1/N is the boxcar up to summation order: each
+    is within 1e-5 cond of the oracle, so they are within 2e-5 cond of each other."""
     w = S.scaled(S.WORKLOADS["multilook_8k"], 64, 96)
-    s = torch.from_numpy(w.image()).cuda()
+    s_np = w.image()
+    s = torch.from_numpy(s_np).cuda()
     a_inv, a_det = zlib.multilook_zinv_det(s, 5, None, 3)
     b_inv, b_det = zlib.multilook_zinv_det(s, 5, torch.full((25,), 1 / 25, device="cuda"), 3)
     torch.cuda.synchronize()
-    assert torch.allclose(a_det, b_det, rtol=1e-5)
+    cond = orc.cond(orc.multilook(s_np, 5))
+    ad, bd = a_det.reshape(-1).cpu().numpy(), b_det.reshape(-1).cpu().numpy()
+    assert np.all(np.abs(ad - bd) <= 2e-5 * cond * np.abs(ad))
 
 
 def test_argument_errors(zlib):
