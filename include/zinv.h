@@ -60,6 +60,7 @@ extern "C" {
 #define ZINV_PLAIN 0u
 #define ZINV_COMPENSATED 1u   /* FMA error-free products and sums in the cofactors and det */
 #define ZINV_FP64_RECOMPUTE 2u /* recompute pixels with det <= tau*a*d*f in FP64 */
+#define ZINV_HOST_STAGED 4u    /* zinv_det_host only: always stage through the workspace */
 
 /* bits of the optional per-pixel status plane */
 #define ZINV_PIX_NOT_PD 1u     /* det <= 0 or not finite: Z is not positive definite */
@@ -213,19 +214,23 @@ int wishart_stat_fwd_noalloc(const float* s1, const float* s2, int64_t H, int64_
                              double* d_loss, void* stream);
 
 /*
- * zinv_det_host -- zinv_det over HOST buffers, streamed through the GPU in
- * chunks (the paper's §4.3: data larger than device memory is fed in pieces,
- * processed and pulled back).  Copies in, kernel and copies out of successive
- * chunks overlap on three streams the library creates once per device.
+ * zinv_det_host -- zinv_det over HOST buffers (the paper's §4.3: data larger than
+ * device memory is fed through the GPU in pieces, processed and pulled back).
+ * When all three host buffers are GPU-accessible (page-locked memory from
+ * cudaHostAlloc or pinned torch tensors, or cudaHostRegister'ed memory) and
+ * ZINV_HOST_STAGED is not set, the kernel reads and writes them directly over
+ * the CPU-GPU link (one launch, no copies; d_ws may be NULL).  Otherwise the
+ * image is staged in chunks through the workspace: copies in, kernel and
+ * copies out of successive chunks overlap on three streams the library creates
+ * once per device.
  *
  *   z_host, zinv_host, det_host  host buffers in the layout above (zinv_host
- *          [9][ld], det_host [n]); page-locked (cudaHostAlloc / pinned torch
- *          tensors) for the copies to be asynchronous.
- *   d_ws, ws_bytes  caller-owned device workspace, at least
+ *          [9][ld], det_host [n]); page-locked for the copies to be asynchronous.
+ *   d_ws, ws_bytes  caller-owned device workspace for the staged way, at least
  *          zinv_det_host_workspace_bytes(chunk) bytes for some chunk >= 1;
  *          the chunk is the largest that fits (a multiple of 4 pixels when
  *          ws_bytes allows).
- *   flags, tau  as zinv_det.
+ *   flags, tau  as zinv_det, plus ZINV_HOST_STAGED.
  * The call is asynchronous with respect to the host and ordered after prior
  * work on `stream`; later work on `stream` waits for the last chunk to land.
  * The host buffers must stay valid until then.  Not re-entrant: two calls on

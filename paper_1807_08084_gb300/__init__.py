@@ -26,6 +26,7 @@ from . import build as _build
 PLAIN = 0
 COMPENSATED = 1
 FP64_RECOMPUTE = 2
+HOST_STAGED = 4
 PIX_NOT_PD = 1
 PIX_RECOMPUTED = 2
 DEFAULT_TAU = 2.0 ** -10
@@ -304,29 +305,32 @@ def zinv_det_host_workspace_bytes(chunk: int) -> int:
     return int(load().zinv_det_host_workspace_bytes(int(chunk)))
 
 
-def zinv_det_host(z_host: torch.Tensor, ws: torch.Tensor, flags: int = PLAIN,
+def zinv_det_host(z_host: torch.Tensor, ws: torch.Tensor | None = None, flags: int = PLAIN,
                   tau: float = DEFAULT_TAU, out: tuple | None = None,
                   device: torch.device | None = None):
-    """zinv_det over pinned host tensors, streamed through the device workspace `ws`
-    (a uint8 CUDA tensor of zinv_det_host_workspace_bytes(chunk) bytes).  Asynchronous:
-    synchronize the current stream before reading the outputs."""
+    """zinv_det over host tensors.  Pinned buffers are processed in place by the
+    kernel over the CPU-GPU link; otherwise (or with HOST_STAGED in flags) the
+    image streams through the device workspace `ws` (a uint8 CUDA tensor of
+    zinv_det_host_workspace_bytes(chunk) bytes).  Asynchronous: synchronize the
+    current stream before reading the outputs."""
     lib = load()
     if z_host.is_cuda or z_host.dtype != torch.float32 or z_host.shape[0] != 9:
         raise ValueError("z_host must be a float32 host tensor of shape [9, ...]")
     if not z_host.is_contiguous():
         raise ValueError("z_host must be contiguous")
     n = z_host[0].numel()
-    if not ws.is_cuda or ws.dtype != torch.uint8:
+    if ws is not None and (not ws.is_cuda or ws.dtype != torch.uint8):
         raise ValueError("ws must be a uint8 CUDA tensor")
     if out is None:
         zinv = torch.empty_like(z_host, pin_memory=True)
         det = torch.empty(z_host.shape[1:], dtype=torch.float32, pin_memory=True)
     else:
         zinv, det = out
-    dev = ws.device if device is None else device
+    dev = (ws.device if ws is not None else torch.device("cuda", torch.cuda.current_device())) \
+        if device is None else device
     with torch.cuda.device(dev):
         rc = lib.zinv_det_host(_ptr(z_host), n, n, _ptr(zinv), _ptr(det), int(flags), float(tau),
-                               _ptr(ws), ws.numel(), _stream(dev))
+                               _ptr(ws), 0 if ws is None else ws.numel(), _stream(dev))
     _check(rc, "zinv_det_host")
     return zinv, det
 

@@ -313,6 +313,13 @@ def test_host_streaming_matches_device(zlib):
     for chunk in (4096, 100_000, n + 10):
         ws = torch.empty(zlib.zinv_det_host_workspace_bytes(chunk), dtype=torch.uint8,
                          device="cuda")
-        zinv_h, det_h = zlib.zinv_det_host(z_pin, ws)
+        zinv_h, det_h = zlib.zinv_det_host(z_pin, ws, zlib.HOST_STAGED)
         torch.cuda.synchronize()
         assert torch.equal(zinv_h, ref_inv.cpu()) and torch.equal(det_h, ref_det.cpu())
+    # pinned buffers without a workspace: the kernel works on host memory directly
+    zinv_h, det_h = zlib.zinv_det_host(z_pin)
+    torch.cuda.synchronize()
+    assert torch.equal(zinv_h, ref_inv.cpu()) and torch.equal(det_h, ref_det.cpu())
+    # pageable input cannot be read by the kernel: it needs the staged way
+    with pytest.raises(RuntimeError):
+        zlib.zinv_det_host(z.clone())
