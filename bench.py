@@ -240,6 +240,8 @@ def main():
     ap.add_argument("--multilook", type=int, default=1, help="also time the fused multilook")
     ap.add_argument("--ml-rows", type=int, default=8192, help="multilook image height")
     ap.add_argument("--wishart", type=int, default=1, help="also time the Wishart statistic")
+    ap.add_argument("--nlm", type=int, default=1, help="also time the nonlocal-means filter")
+    ap.add_argument("--nlm-rows", type=int, default=1024, help="nonlocal-means image side")
     ap.add_argument("--ws-rows", type=int, default=4096, help="Wishart image height")
     ap.add_argument("--rows", type=int, default=16384,
                     help="image height (16384 = the full workload; smaller for profiling)")
@@ -335,6 +337,22 @@ def main():
                                       "frac_hbm": gbs / hbm_peak}
         del sl, ml_inv, ml_det
 
+    # --- nonlocal means, 23 x 23 search window: arithmetic-bound per-pair dets --
+    nlm = {}
+    if args.nlm:
+        wn = S.scaled(S.WORKLOADS["scale_16k"], args.nlm_rows, args.nlm_rows)
+        zn = G.packed_z(wn)
+        zo = torch.empty_like(zn)
+        pairs = wn.n * 23 * 23
+        for name, meth in (("adjugate", zp.NLM_ADJUGATE), ("cholesky", zp.NLM_CHOLESKY)):
+            t = timed(lambda: zp.nlm_wishart(zn, 11, 16.0, 1.0, meth, out=zo), max(3, sub // 5),
+                      args.warmup, world)
+            nlm[name] = {"ms": t, "gpairs_s": pairs / (t * 1e-3) / 1e9}
+        nlm["speedup_adjugate_vs_cholesky"] = nlm["cholesky"]["ms"] / nlm["adjugate"]["ms"]
+        nlm["workload"] = (f"{wn.H}x{wn.W} packed Z (scale_16k generator), radius 11 "
+                           "(23 x 23 window), L = 16, h = 1")
+        del zn, zo
+
     # --- Wishart change statistic (two 4096 x 4096 dates, 7 x 7 window) -------
     wishart = {}
     if args.wishart:
@@ -411,6 +429,7 @@ def main():
             "paths": paths,
             "multilook_8k": multilook or None,
             "wishart_pair_4k": wishart or None,
+            "nlm_23x23": nlm or None,
             "speedup_vs_cholesky": paths["cholesky"]["ms"] / ms,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -155,6 +155,26 @@ int multilook_zinv_det(const float* s, int64_t H, int64_t W, int64_t plane_ld, i
                        float tau, uint8_t* status, int64_t* counts, void* stream);
 
 /*
+ * nlm_wishart -- nonlocal-means filter of a packed covariance image with the
+ * Wishart equal-looks distance, the workload the paper's introduction uses to
+ * motivate fast inversion (§1: for every pixel a 23 x 23 search window of
+ * determinant computations).  For pixels i, j:
+ *     d(i, j) = ln det((Z_i + Z_j)/2) - (ln det Z_i + ln det Z_j)/2   (>= 0),
+ *     w_ij    = exp(-looks * d(i, j) / h)   over the in-image j within `radius`,
+ *     Z'_i    = sum_j w_ij Z_j / sum_j w_ij.
+ * The per-pair determinant is computed by Algorithm 2's cofactor expansion
+ * (method 0) or by Algorithm 1's Cholesky route (method 1), so the two can be
+ * compared where arithmetic sets the time.
+ *
+ *   z       [9][ld] packed input (read only), H x W pixels, positive definite.
+ *   radius  search radius: 1, 2, 3, 5, 7, 11 (23 x 23 window) or 15.
+ *   looks, h  positive and finite.
+ *   z_out   [9][H*W] packed output (plane stride H*W); must not overlap z.
+ */
+int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int radius, float looks,
+                float h, int method, float* z_out, void* stream);
+
+/*
  * Wishart change statistic between two dates with a learnable window (the
  * likelihood-ratio change test the paper lists among the consumers of det Z and
  * Z^-1, §1).  For every pixel p of two co-registered H x W single-look images

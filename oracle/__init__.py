@@ -88,6 +88,11 @@ class Oracle:
         lib.oracle_wishart_bwd_rows.argtypes = [_D, _D, _I64, _I64, _I64, ctypes.c_int, _D,
                                                 ctypes.c_double, _I64, _I64, _D]
         lib.oracle_wishart_bwd_rows.restype = None
+        lib.oracle_pair_distance.argtypes = [_D, _D]
+        lib.oracle_pair_distance.restype = ctypes.c_double
+        lib.oracle_nlm_wishart.argtypes = [_D, _I64, _I64, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, _D]
+        lib.oracle_nlm_wishart.restype = None
         for f in ("oracle_zinv_det", "oracle_det_expansions", "oracle_inverse_full",
                   "oracle_eigvals", "oracle_multilook", "oracle_zinv_det_bwd",
                   "oracle_wishart_fwd", "oracle_wishart_bwd"):
@@ -156,6 +161,18 @@ class Oracle:
         gl = None if g_logdet is None else _f64(g_logdet).reshape(n)
         out = np.empty((9, n))
         self.lib.oracle_zinv_det_bwd(_ptr(z), n, n, _ptr(gz), _ptr(gd), _ptr(gl), _ptr(out))
+        return out
+
+    # -- nonlocal means with the Wishart equal-looks distance (§1) --------
+    def pair_distance(self, zi, zj) -> float:
+        a, b = _f64(zi).reshape(9), _f64(zj).reshape(9)
+        return float(self.lib.oracle_pair_distance(_ptr(a), _ptr(b)))
+
+    def nlm_wishart(self, z, H: int, W: int, radius: int, looks: float, h: float) -> np.ndarray:
+        """z: packed [9, H*W]; returns the filtered packed image [9, H*W]."""
+        z = _f64(z).reshape(9, H * W)
+        out = np.empty((9, H * W))
+        self.lib.oracle_nlm_wishart(_ptr(z), H, W, int(radius), float(looks), float(h), _ptr(out))
         return out
 
     # -- Wishart change statistic ----------------------------------------

@@ -39,6 +39,11 @@
  *   oracle_zinv_det_bwd    real packed gradient of L(W, det, log det) w.r.t. the 9
  *                          packed reals of Z.  Pinned by FP64 central finite
  *                          differences through numpy.linalg.
+ *   oracle_nlm_wishart     nonlocal-means filter of packed Z with the Wishart
+ *                          equal-looks distance over a square search window (§1).
+ *                          Pinned by constant images, h -> infinity (box mean),
+ *                          h -> 0 (identity), d >= 0 with d(i, i) = 0 and
+ *                          symmetry, and brute-force numpy.
  *   oracle_wishart_fwd/bwd change statistic q = ln det Z1 + ln det Z2
  *                          - 2 ln det((Z1+Z2)/2) (the log of the likelihood-ratio
  *                          test the paper cites in §1, divided by the number of
@@ -667,4 +672,60 @@ void oracle_wishart_bwd(const double* s1, const double* s2, int64_t H, int64_t W
                         int64_t plane_ld, int win, const double* w, double g, double* grad_w)
 {
     oracle_wishart_bwd_rows(s1, s2, H, W, plane_ld, win, w, g, 0, H, grad_w);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nonlocal-means filter with a stochastic distance (§1: the paper's         */
+/* motivating workload, 23 x 23 search windows).  For pixels i, j with       */
+/* covariances Z_i, Z_j of the same number of looks L:                       */
+/*     d(i, j) = ln det((Z_i + Z_j)/2) - (ln det Z_i + ln det Z_j)/2  (>= 0), */
+/* the Wishart equal-looks statistic (half the negative log-likelihood ratio */
+/* q of the change test, per look); weights w_ij = exp(-L d(i, j) / h) over  */
+/* the neighbours j inside the image within the search radius, and           */
+/*     Z'_i = sum_j w_ij Z_j / sum_j w_ij.                                   */
+/* ------------------------------------------------------------------------ */
+
+double oracle_pair_distance(const double* zi, const double* zj)
+{
+    mat3 A = unpack(zi, 1, 0), B = unpack(zj, 1, 0), M;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M.m[r][c] = 0.5 * (A.m[r][c] + B.m[r][c]);
+    return logdet(&M) - 0.5 * (logdet(&A) + logdet(&B));
+}
+
+void oracle_nlm_wishart(const double* z, int64_t H, int64_t W, int radius, double looks,
+                        double h, double* out)
+{
+    int64_t n = H * W;
+    double* ld = (double*)malloc((size_t)n * sizeof(double));
+    for (int64_t p = 0; p < n; ++p) {
+        mat3 A = unpack(z, n, p);
+        ld[p] = logdet(&A);
+    }
+    for (int64_t y = 0; y < H; ++y)
+        for (int64_t x = 0; x < W; ++x) {
+            int64_t i = y * W + x;
+            mat3 Zi = unpack(z, n, i);
+            double acc[9] = {0}, wsum = 0.0;
+            for (int dy = -radius; dy <= radius; ++dy)
+                for (int dx = -radius; dx <= radius; ++dx) {
+                    int64_t yy = y + dy, xx = x + dx;
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    int64_t j = yy * W + xx;
+                    mat3 Zj = unpack(z, n, j), M;
+#if ORACLE_MUTANT == 12
+                    double half = 1.0; /* mutant: pair mean without the 1/2 */
+#else
+                    double half = 0.5;
+#endif
+                    for (int r = 0; r < 3; ++r)
+                        for (int c = 0; c < 3; ++c) M.m[r][c] = half * (Zi.m[r][c] + Zj.m[r][c]);
+                    double d = logdet(&M) - 0.5 * (ld[i] + ld[j]);
+                    double w = exp(-looks * d / h);
+                    for (int k = 0; k < 9; ++k) acc[k] += w * z[k * n + j];
+                    wsum += w;
+                }
+            for (int k = 0; k < 9; ++k) out[k * n + i] = acc[k] / wsum;
+        }
+    free(ld);
 }

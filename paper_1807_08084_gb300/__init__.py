@@ -73,6 +73,10 @@ def _declare_extra(lib):
         lib.multilook_zinv_det.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
                                            ctypes.c_uint32, ctypes.c_float, _P, _P, _P]
         lib.multilook_zinv_det.restype = ctypes.c_int
+    if hasattr(lib, "nlm_wishart"):
+        lib.nlm_wishart.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_int, _P, _P]
+        lib.nlm_wishart.restype = ctypes.c_int
     if hasattr(lib, "wishart_stat_fwd"):
         lib.wishart_workspace_bytes.argtypes = [_I64, _I64, ctypes.c_int]
         lib.wishart_workspace_bytes.restype = ctypes.c_size_t
@@ -230,6 +234,29 @@ def multilook_zinv_det(s: torch.Tensor, win: int = 7, weights: torch.Tensor | No
     if want_counts:
         res += (counts,)
     return res
+
+
+NLM_ADJUGATE = 0
+NLM_CHOLESKY = 1
+
+
+def nlm_wishart(z: torch.Tensor, radius: int = 11, looks: float = 16.0, h: float = 1.0,
+                method: int = NLM_ADJUGATE, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Nonlocal-means filter of a packed [9, H, W] image with the Wishart
+    equal-looks distance over a (2 radius + 1)^2 search window; the per-pair
+    determinant by Algorithm 2 (NLM_ADJUGATE) or Algorithm 1 (NLM_CHOLESKY)."""
+    lib = load()
+    if z.dim() != 3:
+        raise ValueError("z must be [9, H, W]")
+    n, ld = _planes(z)
+    H, W = z.shape[1], z.shape[2]
+    if out is None:
+        out = torch.empty((9, H, W), dtype=torch.float32, device=z.device)
+    with torch.cuda.device(z.device):
+        rc = lib.nlm_wishart(_ptr(z), H, W, ld, int(radius), float(looks), float(h), int(method),
+                             _ptr(out), _stream(z.device))
+    _check(rc, "nlm_wishart")
+    return out
 
 
 def wishart_workspace_bytes(H: int, W: int, win: int) -> int:

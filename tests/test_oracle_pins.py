@@ -305,10 +305,55 @@ def check_wishart(o):
     np.testing.assert_allclose(o.wishart_bwd(s1, s2, win, w, -2.5), -2.5 * g, rtol=1e-14)
 
 
+def check_nlm(o):
+    from paper_1807_08084_gb300 import synth as S
+    rng = np.random.default_rng(19)
+    H, W, rad, L = 7, 9, 2, 4.0
+    z = S.scaled(S.WORKLOADS["paper_meas_shaped"], H, W).packed_z().astype(np.float64)
+    A = unpack(z)
+    # distance: d >= 0, d(i, i) = 0, symmetric, against numpy slogdet
+    for _ in range(20):
+        i, j = rng.integers(0, H * W, 2)
+        d = o.pair_distance(z[:, i], z[:, j])
+        ref = (np.linalg.slogdet((A[i] + A[j]) / 2)[1]
+               - 0.5 * (np.linalg.slogdet(A[i])[1] + np.linalg.slogdet(A[j])[1]))
+        assert abs(d - ref) < 1e-12 and d >= -1e-14
+        assert abs(o.pair_distance(z[:, j], z[:, i]) - d) < 1e-14
+        assert abs(o.pair_distance(z[:, i], z[:, i])) < 1e-14
+    # brute force with numpy on a tiny image
+    out = o.nlm_wishart(z, H, W, rad, L, 0.7)
+    ld = np.linalg.slogdet(A)[1]
+    ref = np.empty_like(out)
+    for y in range(H):
+        for x in range(W):
+            i = y * W + x
+            acc, ws = np.zeros(9), 0.0
+            for yy in range(max(0, y - rad), min(H, y + rad + 1)):
+                for xx in range(max(0, x - rad), min(W, x + rad + 1)):
+                    j = yy * W + xx
+                    d = np.linalg.slogdet((A[i] + A[j]) / 2)[1] - 0.5 * (ld[i] + ld[j])
+                    wgt = np.exp(-L * d / 0.7)
+                    acc += wgt * z[:, j]
+                    ws += wgt
+            ref[:, i] = acc / ws
+    np.testing.assert_allclose(out, ref, rtol=1e-11, atol=1e-13)
+    # constant image: unchanged
+    zc = np.repeat(z[:, :1], H * W, axis=1)
+    np.testing.assert_allclose(o.nlm_wishart(zc, H, W, rad, L, 1.0), zc, rtol=1e-13)
+    # h -> infinity: plain mean over the in-image search window
+    big = o.nlm_wishart(z, H, W, rad, L, 1e30)
+    zi = z.reshape(9, H, W)
+    for (y, x) in [(0, 0), (3, 4), (6, 8)]:
+        win = zi[:, max(0, y - rad):y + rad + 1, max(0, x - rad):x + rad + 1].reshape(9, -1)
+        np.testing.assert_allclose(big[:, y * W + x], win.mean(axis=1), rtol=1e-12)
+    # h -> 0: only the pixel itself keeps weight (distinct neighbours)
+    np.testing.assert_allclose(o.nlm_wishart(z, H, W, rad, L, 1e-9), z, rtol=1e-12)
+
+
 CHECKS = [check_sigma_exact, check_random_vs_numpy, check_identity_and_hermitian,
           check_det_properties, check_closed_forms, check_ill_conditioned_det,
           check_multilook_brute,
-          check_bwd_finite_differences, check_wishart]
+          check_bwd_finite_differences, check_wishart, check_nlm]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=lambda c: c.__name__)
@@ -329,6 +374,7 @@ MUTANTS = {
     9: "Jacobi rotation loses the sign of tau",
     10: "gradient sign of the W G W term",
     11: "elimination det ignores the permutation sign",
+    12: "nonlocal means drops the 1/2 of the pair mean",
 }
 
 
