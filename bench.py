@@ -241,6 +241,7 @@ def main():
     ap.add_argument("--ml-rows", type=int, default=8192, help="multilook image height")
     ap.add_argument("--wishart", type=int, default=1, help="also time the Wishart statistic")
     ap.add_argument("--nlm", type=int, default=1, help="also time the nonlocal-means filter")
+    ap.add_argument("--blockdiag", type=int, default=1, help="also time 3-band block-diagonal pixels")
     ap.add_argument("--nlm-rows", type=int, default=1024, help="nonlocal-means image side")
     ap.add_argument("--ws-rows", type=int, default=4096, help="Wishart image height")
     ap.add_argument("--rows", type=int, default=16384,
@@ -337,6 +338,19 @@ def main():
                                       "frac_hbm": gbs / hbm_peak}
         del sl, ml_inv, ml_det
 
+    # --- multifrequency: three bands, block-diagonal pixels (8192 x 8192) -------
+    blockdiag = {}
+    if args.blockdiag:
+        from dataclasses import replace as _replace
+        wb = S.scaled(S.WORKLOADS["scale_16k"], 8192, 8192)
+        zb = torch.stack([G.packed_z(_replace(wb, seed=wb.seed + 17 * b)) for b in range(3)])
+        t = timed(lambda: zp.zinv_det_blockdiag(zb), sub, args.warmup, world)
+        gbs = (3 * 72 + 4) * wb.n / (t * 1e-3) / 1e9
+        blockdiag = {"ms": t, "gpix_s": wb.n / (t * 1e-3) / 1e9, "gbs": gbs,
+                     "frac_hbm": gbs / hbm_peak,
+                     "workload": "8192x8192 pixels x 3 bands of packed Z (scale_16k generator)"}
+        del zb
+
     # --- nonlocal means, 23 x 23 search window: arithmetic-bound per-pair dets --
     nlm = {}
     if args.nlm:
@@ -430,6 +444,7 @@ def main():
             "multilook_8k": multilook or None,
             "wishart_pair_4k": wishart or None,
             "nlm_23x23": nlm or None,
+            "blockdiag_3band": blockdiag or None,
             "speedup_vs_cholesky": paths["cholesky"]["ms"] / ms,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -109,6 +109,20 @@ int chol_zinv_det(const float* z, int64_t n, int64_t ld, float* zinv, float* det
                   uint32_t flags, float tau, uint8_t* status, int64_t* counts, void* stream);
 
 /*
+ * zinv_det_blockdiag -- multifrequency pixels (§5: with several bands the
+ * matrices are block diagonal, each block Hermitian, and inverse and
+ * determinant follow from Algorithm 2 applied to each diagonal block).  Pixel p
+ * has nblocks (1..8) packed 3x3 blocks: block b's plane k at
+ * z[(b*9 + k)*ld + p].  Outputs: zinv in the same layout (the diagonal blocks of
+ * the inverse; the off-diagonal blocks are zero), det[p] = product of the
+ * blocks' determinants.  flags, tau, status (OR over the blocks) and counts as
+ * zinv_det; 128-bit path under the same alignment conditions.
+ */
+int zinv_det_blockdiag(const float* z, int nblocks, int64_t n, int64_t ld, float* zinv,
+                       float* det, uint32_t flags, float tau, uint8_t* status, int64_t* counts,
+                       void* stream);
+
+/*
  * zinv_det_bwd -- backward of (Z^-1, det, log det) w.r.t. the nine packed reals
  * of Z, from the forward's saved outputs W = Z^-1 and det.  With G the
  * Hermitian matrix of the upstream packed gradient (G_ii = g_ii,

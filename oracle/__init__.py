@@ -88,6 +88,8 @@ class Oracle:
         lib.oracle_wishart_bwd_rows.argtypes = [_D, _D, _I64, _I64, _I64, ctypes.c_int, _D,
                                                 ctypes.c_double, _I64, _I64, _D]
         lib.oracle_wishart_bwd_rows.restype = None
+        lib.oracle_zinv_det_blockdiag.argtypes = [_D, ctypes.c_int, _I64, _I64, _D, _D, _D]
+        lib.oracle_zinv_det_blockdiag.restype = None
         lib.oracle_pair_distance.argtypes = [_D, _D]
         lib.oracle_pair_distance.restype = ctypes.c_double
         lib.oracle_nlm_wishart.argtypes = [_D, _I64, _I64, ctypes.c_int, ctypes.c_double,
@@ -162,6 +164,17 @@ class Oracle:
         out = np.empty((9, n))
         self.lib.oracle_zinv_det_bwd(_ptr(z), n, n, _ptr(gz), _ptr(gd), _ptr(gl), _ptr(out))
         return out
+
+    # -- multifrequency block-diagonal pixels (§5) ------------------------
+    def zinv_det_blockdiag(self, z, nb: int):
+        """z: [nb, 9, n] packed blocks -> (zinv [nb, 9, n], det [n], off-block max [n])."""
+        z = _f64(z).reshape(nb, 9, -1)
+        n = z.shape[2]
+        zinv = np.empty((nb, 9, n))
+        det = np.empty(n)
+        off = np.empty(n)
+        self.lib.oracle_zinv_det_blockdiag(_ptr(z), int(nb), n, n, _ptr(zinv), _ptr(det), _ptr(off))
+        return zinv, det, off
 
     # -- nonlocal means with the Wishart equal-looks distance (§1) --------
     def pair_distance(self, zi, zj) -> float:

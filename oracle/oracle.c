@@ -39,6 +39,9 @@
  *   oracle_zinv_det_bwd    real packed gradient of L(W, det, log det) w.r.t. the 9
  *                          packed reals of Z.  Pinned by FP64 central finite
  *                          differences through numpy.linalg.
+ *   oracle_zinv_det_blockdiag  multifrequency block-diagonal pixels (§5): GE on the
+ *                          full 3nb x 3nb matrix.  Pinned by numpy.linalg on the
+ *                          full matrix and by the product of the blocks' dets.
  *   oracle_nlm_wishart     nonlocal-means filter of packed Z with the Wishart
  *                          equal-looks distance over a square search window (§1).
  *                          Pinned by constant images, h -> infinity (box mean),
@@ -728,4 +731,96 @@ void oracle_nlm_wishart(const double* z, int64_t H, int64_t W, int radius, doubl
             for (int k = 0; k < 9; ++k) out[k * n + i] = acc[k] / wsum;
         }
     free(ld);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multifrequency data (§5): per pixel a block-diagonal Hermitian matrix of  */
+/* nb 3x3 Hermitian blocks.  The oracle inverts the full 3nb x 3nb matrix by */
+/* Gauss-Jordan elimination with partial pivoting and takes its det from     */
+/* the pivots -- the plain definition, which does not use the block         */
+/* structure -- and returns the diagonal blocks of the inverse (packed) and  */
+/* the largest modulus found off the diagonal blocks (zero in exact          */
+/* arithmetic).                                                             */
+/* ------------------------------------------------------------------------ */
+
+#define ORACLE_MAX_BLOCKS 8
+
+static int ge_inverse_n(int m, const cplx* A, cplx* X, cplx* det)
+{
+    cplx M[3 * ORACLE_MAX_BLOCKS][6 * ORACLE_MAX_BLOCKS];
+    cplx prod = 1.0;
+    int swaps = 0;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            M[i][j] = A[i * m + j];
+            M[i][m + j] = (i == j) ? 1.0 : 0.0;
+        }
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+            if (cabs(M[r][col]) > cabs(M[piv][col])) piv = r;
+        if (cabs(M[piv][col]) == 0.0) {
+            *det = 0.0;
+            return -1;
+        }
+        if (piv != col) {
+            ++swaps;
+            for (int k = 0; k < 2 * m; ++k) {
+                cplx t = M[col][k];
+                M[col][k] = M[piv][k];
+                M[piv][k] = t;
+            }
+        }
+        prod *= M[col][col];
+        cplx inv_p = 1.0 / M[col][col];
+        for (int k = 0; k < 2 * m; ++k) M[col][k] *= inv_p;
+        for (int r = 0; r < m; ++r) {
+            if (r == col) continue;
+            cplx factor = M[r][col];
+            for (int k = 0; k < 2 * m; ++k) M[r][k] -= factor * M[col][k];
+        }
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) X[i * m + j] = M[i][m + j];
+    *det = (swaps % 2) ? -prod : prod;
+    return 0;
+}
+
+/*
+ * z: [nb][9][ld] packed blocks; zinv: [nb][9][n] packed diagonal blocks of the
+ * full inverse; det: [n] det of the full matrix; off: [n] max |entry| of the
+ * full inverse outside the diagonal blocks.
+ */
+void oracle_zinv_det_blockdiag(const double* z, int nb, int64_t n, int64_t ld, double* zinv,
+                               double* det, double* off)
+{
+    int m = 3 * nb;
+    cplx A[9 * ORACLE_MAX_BLOCKS * ORACLE_MAX_BLOCKS], X[9 * ORACLE_MAX_BLOCKS * ORACLE_MAX_BLOCKS];
+    for (int64_t p = 0; p < n; ++p) {
+        for (int i = 0; i < m * m; ++i) A[i] = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            mat3 B = unpack(z + (int64_t)b * 9 * ld, ld, p);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) A[(3 * b + i) * m + 3 * b + j] = B.m[i][j];
+        }
+        cplx dt;
+        if (ge_inverse_n(m, A, X, &dt) != 0) {
+            for (int b = 0; b < nb; ++b) fill_nan(zinv + (int64_t)b * 9 * n, n, p, 9);
+            det[p] = 0.0;
+            off[p] = NAN;
+            continue;
+        }
+        det[p] = creal(dt);
+        double mx = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j)
+                if (i / 3 != j / 3 && cabs(X[i * m + j]) > mx) mx = cabs(X[i * m + j]);
+        off[p] = mx;
+        for (int b = 0; b < nb; ++b) {
+            mat3 Y;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) Y.m[i][j] = X[(3 * b + i) * m + 3 * b + j];
+            pack_upper(&Y, zinv + (int64_t)b * 9 * n, n, p);
+        }
+    }
 }

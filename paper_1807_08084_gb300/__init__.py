@@ -73,6 +73,10 @@ def _declare_extra(lib):
         lib.multilook_zinv_det.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
                                            ctypes.c_uint32, ctypes.c_float, _P, _P, _P]
         lib.multilook_zinv_det.restype = ctypes.c_int
+    if hasattr(lib, "zinv_det_blockdiag"):
+        lib.zinv_det_blockdiag.argtypes = [_P, ctypes.c_int, _I64, _I64, _P, _P, ctypes.c_uint32,
+                                           ctypes.c_float, _P, _P, _P]
+        lib.zinv_det_blockdiag.restype = ctypes.c_int
     if hasattr(lib, "nlm_wishart"):
         lib.nlm_wishart.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_int, _P, _P]
@@ -228,6 +232,34 @@ def multilook_zinv_det(s: torch.Tensor, win: int = 7, weights: torch.Tensor | No
                                     _ptr(det), int(flags), float(tau), _ptr(status), _ptr(counts),
                                     _stream(s.device))
     _check(rc, "multilook_zinv_det")
+    res = (zinv, det)
+    if want_status:
+        res += (status,)
+    if want_counts:
+        res += (counts,)
+    return res
+
+
+def zinv_det_blockdiag(z: torch.Tensor, flags: int = PLAIN, tau: float = DEFAULT_TAU,
+                       want_status: bool = False, want_counts: bool = False):
+    """Multifrequency pixels: z float32 [nb, 9, ...] (nb diagonal 3x3 blocks per pixel).
+    Returns (the blocks' inverses, shaped like z; det = product over blocks) [+ status]
+    [+ counts]."""
+    lib = load()
+    if not z.is_cuda or z.dtype != torch.float32 or z.dim() < 3 or z.shape[1] != 9:
+        raise ValueError("z must be a float32 CUDA tensor of shape [nb, 9, ...]")
+    if not z.is_contiguous():
+        raise ValueError("z must be contiguous")
+    nb = z.shape[0]
+    n = z[0, 0].numel()
+    zinv = torch.empty_like(z)
+    det = torch.empty(z.shape[2:], dtype=torch.float32, device=z.device)
+    status = torch.empty(z.shape[2:], dtype=torch.uint8, device=z.device) if want_status else None
+    counts = torch.empty(2, dtype=torch.int64, device=z.device) if want_counts else None
+    with torch.cuda.device(z.device):
+        rc = lib.zinv_det_blockdiag(_ptr(z), nb, n, n, _ptr(zinv), _ptr(det), int(flags),
+                                    float(tau), _ptr(status), _ptr(counts), _stream(z.device))
+    _check(rc, "zinv_det_blockdiag")
     res = (zinv, det)
     if want_status:
         res += (status,)
