@@ -59,20 +59,6 @@ bool device_accessible(const void* p) {
   }
 }
 
-int64_t grid_blocks(const void* kernel, int threads, size_t smem, int64_t items,
-                    const DeviceInfo& di) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
-          cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
-  const int64_t wave = (int64_t)per_sm * di.sm_count;
-  const int64_t need = (items + threads - 1) / threads;
-  return need < wave ? (need > 0 ? need : 1) : wave;
-}
-
 }  // namespace zinv
 
 extern "C" int zinv_abi_version(void) { return ZINV_ABI_VERSION; }

@@ -103,24 +103,24 @@ __global__ void __launch_bounds__(kBT) k_blockdiag_scalar(BdArgs a) {
 }
 
 template <int ALG, bool STAT>
-int launch_bd(const BdArgs& a, cudaStream_t s, const DeviceInfo& di) {
+int launch_bd(const BdArgs& a, cudaStream_t s) {
   const bool vec = (a.ld % 4 == 0) && aligned(a.z, 16) && aligned(a.zinv, 16) &&
                    aligned(a.det, 16) && (a.status == nullptr || aligned(a.status, 4));
   if (vec) {
     auto k = k_blockdiag_vec4<ALG, STAT>;
     const int64_t items = (a.n >> 2) > 0 ? (a.n >> 2) : 1;
-    k<<<(unsigned)grid_blocks((const void*)k, kBT, 0, items, di), kBT, 0, s>>>(a);
+    k<<<(unsigned)cover_blocks(items, kBT), kBT, 0, s>>>(a);
   } else {
     auto k = k_blockdiag_scalar<ALG, STAT>;
-    k<<<(unsigned)grid_blocks((const void*)k, kBT, 0, a.n, di), kBT, 0, s>>>(a);
+    k<<<(unsigned)cover_blocks(a.n, kBT), kBT, 0, s>>>(a);
   }
   return launch_status();
 }
 
 template <int ALG>
-int dispatch_bd(const BdArgs& a, cudaStream_t s, const DeviceInfo& di) {
-  if (a.status || a.counts) return launch_bd<ALG, true>(a, s, di);
-  return launch_bd<ALG, false>(a, s, di);
+int dispatch_bd(const BdArgs& a, cudaStream_t s) {
+  if (a.status || a.counts) return launch_bd<ALG, true>(a, s);
+  return launch_bd<ALG, false>(a, s);
 }
 
 }  // namespace
@@ -154,10 +154,10 @@ extern "C" int zinv_det_blockdiag(const float* z, int nblocks, int64_t n, int64_
   if (n == 0) return ZINV_OK;
   BdArgs a{z, zinv, det, status, cnt, n, ld, nblocks, tau};
   switch (alg) {
-    case kPlain: return dispatch_bd<kPlain>(a, s, di);
-    case kComp: return dispatch_bd<kComp>(a, s, di);
-    case kPlainF64: return dispatch_bd<kPlainF64>(a, s, di);
-    case kCompF64: return dispatch_bd<kCompF64>(a, s, di);
+    case kPlain: return dispatch_bd<kPlain>(a, s);
+    case kComp: return dispatch_bd<kComp>(a, s);
+    case kPlainF64: return dispatch_bd<kPlainF64>(a, s);
+    case kCompF64: return dispatch_bd<kCompF64>(a, s);
   }
   return ZINV_ERR_ARG;
 }

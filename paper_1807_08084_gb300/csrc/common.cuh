@@ -26,11 +26,19 @@ int device_info(DeviceInfo* out, int* dev_out = nullptr);
 // True when the GPU can dereference p (device, managed, or mapped host memory).
 bool device_accessible(const void* p);
 
-// Blocks for a grid-stride kernel: enough to cover `items` work items at
-// `threads` per block, capped at (resident blocks per SM) x (SM count) so the
-// grid is a whole number of waves over the 152 SMs.
-int64_t grid_blocks(const void* kernel, int threads, size_t smem, int64_t items,
-                    const DeviceInfo& di);
+// Blocks covering `items` work items at `threads` per block and `per_thread`
+// items per thread (every kernel here keeps a grid-stride loop, so any grid
+// size stays correct).  The hardware block scheduler then walks memory in
+// order and backfills each SM as its blocks finish.  On GB300 a covering grid
+// streamed ~8% faster than a persistent one-wave grid-stride launch of the
+// same kernel (7.0 vs 6.45 TB/s); kernels heavy in registers and arithmetic
+// gain from a few items per thread (fewer block launches per SM).
+inline int64_t cover_blocks(int64_t items, int threads, int per_thread = 1) {
+  const int64_t span = (int64_t)threads * per_thread;
+  int64_t b = (items + span - 1) / span;
+  if (b < 1) b = 1;
+  return b > 2147483647 ? 2147483647 : b;
+}
 
 inline bool aligned(const void* p, uintptr_t a) {
   return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0;

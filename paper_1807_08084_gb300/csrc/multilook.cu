@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kMlThreads) k_multilook_weighted(MlArgs a) {
 }
 
 template <typename K>
-int launch_ml(K kernel, size_t smem, const MlArgs& a, cudaStream_t s, const DeviceInfo& di) {
+int launch_ml(K kernel, size_t smem, const MlArgs& a, cudaStream_t s) {
   static_assert(sizeof(K) > 0, "");
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
@@ -412,40 +412,40 @@ int launch_ml(K kernel, size_t smem, const MlArgs& a, cudaStream_t s, const Devi
     return ZINV_ERR_LAUNCH;
   }
   const int64_t tiles = ((a.W + kTW - 1) / kTW) * ((a.H + kTH - 1) / kTH);
-  const int64_t blocks = grid_blocks((const void*)kernel, kMlThreads, smem, tiles * kMlThreads, di);
+  const int64_t blocks = cover_blocks(tiles * kMlThreads, kMlThreads);
   kernel<<<(unsigned)blocks, kMlThreads, smem, s>>>(a);
   return launch_status();
 }
 
 template <typename K>
-int launch_strip(K kernel, size_t smem, const MlArgs& a, cudaStream_t s, const DeviceInfo& di) {
+int launch_strip(K kernel, size_t smem, const MlArgs& a, cudaStream_t s) {
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return ZINV_ERR_LAUNCH;
   }
   const int64_t units = ((a.W + kTW - 1) / kTW) * ((a.H + kSeg - 1) / kSeg);
-  const int64_t blocks = grid_blocks((const void*)kernel, kSThreads, smem, units * kSThreads, di);
+  const int64_t blocks = cover_blocks(units * kSThreads, kSThreads);
   kernel<<<(unsigned)blocks, kSThreads, smem, s>>>(a);
   return launch_status();
 }
 
 template <int ALG, bool STAT>
-int dispatch_ml(const MlArgs& a, cudaStream_t s, const DeviceInfo& di) {
+int dispatch_ml(const MlArgs& a, cudaStream_t s) {
   if (a.weights)
-    return launch_ml(k_multilook_weighted<ALG, STAT>, kWSmem, a, s, di);
+    return launch_ml(k_multilook_weighted<ALG, STAT>, kWSmem, a, s);
   switch (a.win) {
-    case 3: return launch_strip(k_multilook_strip<1, ALG, STAT>, Strip<1>::smem, a, s, di);
-    case 5: return launch_strip(k_multilook_strip<2, ALG, STAT>, Strip<2>::smem, a, s, di);
-    case 7: return launch_strip(k_multilook_strip<3, ALG, STAT>, Strip<3>::smem, a, s, di);
+    case 3: return launch_strip(k_multilook_strip<1, ALG, STAT>, Strip<1>::smem, a, s);
+    case 5: return launch_strip(k_multilook_strip<2, ALG, STAT>, Strip<2>::smem, a, s);
+    case 7: return launch_strip(k_multilook_strip<3, ALG, STAT>, Strip<3>::smem, a, s);
   }
   return ZINV_ERR_ARG;
 }
 
 template <int ALG>
-int dispatch_ml_stat(const MlArgs& a, cudaStream_t s, const DeviceInfo& di) {
-  if (a.status || a.counts) return dispatch_ml<ALG, true>(a, s, di);
-  return dispatch_ml<ALG, false>(a, s, di);
+int dispatch_ml_stat(const MlArgs& a, cudaStream_t s) {
+  if (a.status || a.counts) return dispatch_ml<ALG, true>(a, s);
+  return dispatch_ml<ALG, false>(a, s);
 }
 
 }  // namespace
@@ -486,10 +486,10 @@ extern "C" int multilook_zinv_det(const float* s, int64_t H, int64_t W, int64_t 
   MlArgs a{reinterpret_cast<const float2*>(s), H, W, plane_ld, zinv, det, tau, status, cnt,
            weights, win};
   switch (alg) {
-    case kPlain: return dispatch_ml_stat<kPlain>(a, st, di);
-    case kComp: return dispatch_ml_stat<kComp>(a, st, di);
-    case kPlainF64: return dispatch_ml_stat<kPlainF64>(a, st, di);
-    case kCompF64: return dispatch_ml_stat<kCompF64>(a, st, di);
+    case kPlain: return dispatch_ml_stat<kPlain>(a, st);
+    case kComp: return dispatch_ml_stat<kComp>(a, st);
+    case kPlainF64: return dispatch_ml_stat<kPlainF64>(a, st);
+    case kCompF64: return dispatch_ml_stat<kCompF64>(a, st);
   }
   return ZINV_ERR_ARG;
 }

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kNT) k_nlm(NlmArgs a) {
 }
 
 template <int METHOD, int RAD>
-int launch_nlm(const NlmArgs& a, cudaStream_t s, const DeviceInfo& di) {
+int launch_nlm(const NlmArgs& a, cudaStream_t s) {
   constexpr int SW = kNW + 2 * RAD, SH = kNH + 2 * RAD;
   const size_t smem = (size_t)10 * SH * SW * sizeof(float);
   auto k = k_nlm<METHOD, RAD>;
@@ -148,21 +148,21 @@ int launch_nlm(const NlmArgs& a, cudaStream_t s, const DeviceInfo& di) {
     return ZINV_ERR_LAUNCH;
   }
   const int64_t tiles = ((a.W + kNW - 1) / kNW) * ((a.H + kNH - 1) / kNH);
-  const int64_t blocks = grid_blocks((const void*)k, kNT, smem, tiles * kNT, di);
+  const int64_t blocks = cover_blocks(tiles * kNT, kNT);
   k<<<(unsigned)blocks, kNT, smem, s>>>(a);
   return launch_status();
 }
 
 template <int METHOD>
-int dispatch_nlm(const NlmArgs& a, cudaStream_t s, const DeviceInfo& di) {
+int dispatch_nlm(const NlmArgs& a, cudaStream_t s) {
   switch (a.radius) {
-    case 1: return launch_nlm<METHOD, 1>(a, s, di);
-    case 2: return launch_nlm<METHOD, 2>(a, s, di);
-    case 3: return launch_nlm<METHOD, 3>(a, s, di);
-    case 5: return launch_nlm<METHOD, 5>(a, s, di);
-    case 7: return launch_nlm<METHOD, 7>(a, s, di);
-    case 11: return launch_nlm<METHOD, 11>(a, s, di);
-    case 15: return launch_nlm<METHOD, 15>(a, s, di);
+    case 1: return launch_nlm<METHOD, 1>(a, s);
+    case 2: return launch_nlm<METHOD, 2>(a, s);
+    case 3: return launch_nlm<METHOD, 3>(a, s);
+    case 5: return launch_nlm<METHOD, 5>(a, s);
+    case 7: return launch_nlm<METHOD, 7>(a, s);
+    case 11: return launch_nlm<METHOD, 11>(a, s);
+    case 15: return launch_nlm<METHOD, 15>(a, s);
   }
   return ZINV_ERR_ARG;
 }
@@ -186,5 +186,5 @@ extern "C" int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int
   if (!device_accessible(z) || !device_accessible(z_out)) return ZINV_ERR_ARG;
   NlmArgs a{z, H, W, ld, radius, -looks / (h * 0.69314718055994531f), z_out};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return method == 0 ? dispatch_nlm<0>(a, s, di) : dispatch_nlm<1>(a, s, di);
+  return method == 0 ? dispatch_nlm<0>(a, s) : dispatch_nlm<1>(a, s);
 }

@@ -371,14 +371,14 @@ int64_t tile_count(int64_t H, int64_t W) {
 }
 
 template <typename Kern>
-int launch_tiles(Kern kernel, size_t smem, const WsArgs& a, cudaStream_t s, const DeviceInfo& di) {
+int launch_tiles(Kern kernel, size_t smem, const WsArgs& a, cudaStream_t s) {
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return ZINV_ERR_LAUNCH;
   }
   const int64_t tiles = tile_count(a.H, a.W);
-  const int64_t blocks = grid_blocks((const void*)kernel, kWT, smem, tiles * kWT, di);
+  const int64_t blocks = cover_blocks(tiles * kWT, kWT);
   kernel<<<(unsigned)blocks, kWT, smem, s>>>(a);
   return launch_status();
 }
@@ -431,9 +431,9 @@ extern "C" int wishart_stat_fwd(const float* s1, const float* s2, int64_t H, int
   a.q_map = q_map;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (win) {
-    case 3: rc = launch_tiles(k_wishart_fwd<1>, fwd_smem<1>(), a, st, di); break;
-    case 5: rc = launch_tiles(k_wishart_fwd<2>, fwd_smem<2>(), a, st, di); break;
-    default: rc = launch_tiles(k_wishart_fwd<3>, fwd_smem<3>(), a, st, di); break;
+    case 3: rc = launch_tiles(k_wishart_fwd<1>, fwd_smem<1>(), a, st); break;
+    case 5: rc = launch_tiles(k_wishart_fwd<2>, fwd_smem<2>(), a, st); break;
+    default: rc = launch_tiles(k_wishart_fwd<3>, fwd_smem<3>(), a, st); break;
   }
   if (rc != ZINV_OK) return rc;
   k_reduce_tiles<<<1, kRedThreads, 0, st>>>(a.partial, tile_count(H, W), 1, nullptr, d_loss, 1);
@@ -455,9 +455,9 @@ extern "C" int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int
     return ZINV_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (win) {
-    case 3: rc = launch_tiles(k_wishart_bwd<1>, bwd_smem<1>(), a, st, di); break;
-    case 5: rc = launch_tiles(k_wishart_bwd<2>, bwd_smem<2>(), a, st, di); break;
-    default: rc = launch_tiles(k_wishart_bwd<3>, bwd_smem<3>(), a, st, di); break;
+    case 3: rc = launch_tiles(k_wishart_bwd<1>, bwd_smem<1>(), a, st); break;
+    case 5: rc = launch_tiles(k_wishart_bwd<2>, bwd_smem<2>(), a, st); break;
+    default: rc = launch_tiles(k_wishart_bwd<3>, bwd_smem<3>(), a, st); break;
   }
   if (rc != ZINV_OK) return rc;
   k_reduce_tiles<<<win * win, kRedThreads, 0, st>>>(a.partial, tile_count(H, W), win * win,
@@ -526,9 +526,9 @@ extern "C" int wishart_stat_fwd_noalloc(const float* s1, const float* s2, int64_
   a.partial = sc.ptr;  // every tile writes its own slot before the reduce reads it
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (win) {
-    case 3: rc = launch_tiles(k_wishart_fwd<1>, fwd_smem<1>(), a, st, di); break;
-    case 5: rc = launch_tiles(k_wishart_fwd<2>, fwd_smem<2>(), a, st, di); break;
-    default: rc = launch_tiles(k_wishart_fwd<3>, fwd_smem<3>(), a, st, di); break;
+    case 3: rc = launch_tiles(k_wishart_fwd<1>, fwd_smem<1>(), a, st); break;
+    case 5: rc = launch_tiles(k_wishart_fwd<2>, fwd_smem<2>(), a, st); break;
+    default: rc = launch_tiles(k_wishart_fwd<3>, fwd_smem<3>(), a, st); break;
   }
   if (rc != ZINV_OK) return rc;
   k_reduce_tiles<<<1, kRedThreads, 0, st>>>(a.partial, tiles, 1, nullptr, d_loss, 1);

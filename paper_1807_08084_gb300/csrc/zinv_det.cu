@@ -5,16 +5,25 @@
 // FP32 operations.  Layout is planar SoA, so a warp's access to one plane is
 // one contiguous run.  The main kernel gives each thread four consecutive
 // pixels: nine 128-bit streaming loads (one per plane), the arithmetic on four
-// independent pixels, ten 128-bit streaming stores.  The grid is a whole
-// number of waves (resident blocks x SMs) striding over the image.  Pixels
-// that do not fill a float4 (n % 4) and unaligned layouts take the one-pixel-
-// per-thread kernel, still coalesced.
+// independent pixels, ten 128-bit streaming stores.  The grid covers the
+// image (see kGroupsPerThread for the per-variant split), which streamed
+// faster than a persistent grid.  Pixels that do not fill a float4 (n % 4) and
+// unaligned layouts take the one-pixel-per-thread kernel, still coalesced.
 #include "common.cuh"
 #include "pixel.cuh"
 
 namespace zinv {
 
 constexpr int kThreads = 256;
+
+// Launch shape per variant, from a sweep on GB300 over a 16384 x 16384 image.
+// The light variants stream best with one group of four pixels per thread.
+// The compensated ones hold more registers and arithmetic per group and run
+// best with several groups per thread: 32 for compensated (3.21 -> 3.02 ms),
+// 16 for compensated + FP64, whose register cap for three blocks per SM (at
+// the cost of some spills) took it from 4.22 to 3.43 ms.
+template <int ALG>
+constexpr int kGroupsPerThread = ALG == kComp ? 32 : ALG == kCompF64 ? 16 : 1;
 
 template <int ALG, bool STAT>
 __device__ __forceinline__ void one_pixel(const float* __restrict__ z, int64_t ld, int64_t p,
@@ -36,10 +45,10 @@ __device__ __forceinline__ void one_pixel(const float* __restrict__ z, int64_t l
 }
 
 template <int ALG, bool STAT>
-__global__ void __launch_bounds__(kThreads)
-    k_inv_det_vec4(const float* __restrict__ z, int64_t n, int64_t ld, float* __restrict__ zinv,
-                   float* __restrict__ det, float tau, uint8_t* __restrict__ status,
-                   unsigned long long* __restrict__ counts) {
+__device__ __forceinline__ void inv_det_vec4(const float* __restrict__ z, int64_t n, int64_t ld,
+                                             float* __restrict__ zinv, float* __restrict__ det,
+                                             float tau, uint8_t* __restrict__ status,
+                                             unsigned long long* __restrict__ counts) {
   const int64_t groups = n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   uint32_t c0 = 0, c1 = 0;
@@ -77,6 +86,23 @@ __global__ void __launch_bounds__(kThreads)
 
 template <int ALG, bool STAT>
 __global__ void __launch_bounds__(kThreads)
+    k_inv_det_vec4(const float* __restrict__ z, int64_t n, int64_t ld, float* __restrict__ zinv,
+                   float* __restrict__ det, float tau, uint8_t* __restrict__ status,
+                   unsigned long long* __restrict__ counts) {
+  inv_det_vec4<ALG, STAT>(z, n, ld, zinv, det, tau, status, counts);
+}
+
+// Compensated + FP64 recompute, held to three blocks per SM.
+template <bool STAT>
+__global__ void __launch_bounds__(kThreads, 3)
+    k_inv_det_vec4_c64(const float* __restrict__ z, int64_t n, int64_t ld,
+                       float* __restrict__ zinv, float* __restrict__ det, float tau,
+                       uint8_t* __restrict__ status, unsigned long long* __restrict__ counts) {
+  inv_det_vec4<kCompF64, STAT>(z, n, ld, zinv, det, tau, status, counts);
+}
+
+template <int ALG, bool STAT>
+__global__ void __launch_bounds__(kThreads)
     k_inv_det_scalar(const float* __restrict__ z, int64_t n, int64_t ld, float* __restrict__ zinv,
                      float* __restrict__ det, float tau, uint8_t* __restrict__ status,
                      unsigned long long* __restrict__ counts) {
@@ -90,29 +116,32 @@ __global__ void __launch_bounds__(kThreads)
 template <int ALG, bool STAT>
 static int launch_inv_det(const float* z, int64_t n, int64_t ld, float* zinv, float* det,
                           float tau, uint8_t* status, unsigned long long* counts,
-                          cudaStream_t s, const DeviceInfo& di) {
+                          cudaStream_t s) {
   const bool vec = (ld % 4 == 0) && aligned(z, 16) && aligned(zinv, 16) && aligned(det, 16) &&
                    (status == nullptr || aligned(status, 4));
   if (vec) {
-    auto k = k_inv_det_vec4<ALG, STAT>;
     const int64_t items = (n >> 2) > 0 ? (n >> 2) : 1;
-    const int64_t blocks = grid_blocks((const void*)k, kThreads, 0, items, di);
-    k<<<(unsigned)blocks, kThreads, 0, s>>>(z, n, ld, zinv, det, tau, status, counts);
+    const unsigned blocks = (unsigned)cover_blocks(items, kThreads, kGroupsPerThread<ALG>);
+    if constexpr (ALG == kCompF64)
+      k_inv_det_vec4_c64<STAT><<<blocks, kThreads, 0, s>>>(z, n, ld, zinv, det, tau, status,
+                                                           counts);
+    else
+      k_inv_det_vec4<ALG, STAT><<<blocks, kThreads, 0, s>>>(z, n, ld, zinv, det, tau, status,
+                                                            counts);
   } else {
     auto k = k_inv_det_scalar<ALG, STAT>;
-    const int64_t blocks = grid_blocks((const void*)k, kThreads, 0, n, di);
-    k<<<(unsigned)blocks, kThreads, 0, s>>>(z, n, ld, zinv, det, tau, status, counts);
+    k<<<(unsigned)cover_blocks(n, kThreads), kThreads, 0, s>>>(z, n, ld, zinv, det, tau, status,
+                                                               counts);
   }
   return launch_status();
 }
 
 template <int ALG>
 static int dispatch_stat(const float* z, int64_t n, int64_t ld, float* zinv, float* det,
-                         float tau, uint8_t* status, unsigned long long* counts, cudaStream_t s,
-                         const DeviceInfo& di) {
+                         float tau, uint8_t* status, unsigned long long* counts, cudaStream_t s) {
   if (status || counts)
-    return launch_inv_det<ALG, true>(z, n, ld, zinv, det, tau, status, counts, s, di);
-  return launch_inv_det<ALG, false>(z, n, ld, zinv, det, tau, status, counts, s, di);
+    return launch_inv_det<ALG, true>(z, n, ld, zinv, det, tau, status, counts, s);
+  return launch_inv_det<ALG, false>(z, n, ld, zinv, det, tau, status, counts, s);
 }
 
 // Shared argument checks of zinv_det / chol_zinv_det: sizes and pointer
@@ -150,13 +179,13 @@ int inv_det_entry(int alg, const float* z, int64_t n, int64_t ld, float* zinv, f
     return ZINV_ERR_LAUNCH;
   if (n == 0) return ZINV_OK;
   switch (alg) {
-    case kPlain: return dispatch_stat<kPlain>(z, n, ld, zinv, det, tau, status, cnt, s, di);
-    case kComp: return dispatch_stat<kComp>(z, n, ld, zinv, det, tau, status, cnt, s, di);
+    case kPlain: return dispatch_stat<kPlain>(z, n, ld, zinv, det, tau, status, cnt, s);
+    case kComp: return dispatch_stat<kComp>(z, n, ld, zinv, det, tau, status, cnt, s);
     case kPlainF64:
-      return dispatch_stat<kPlainF64>(z, n, ld, zinv, det, tau, status, cnt, s, di);
+      return dispatch_stat<kPlainF64>(z, n, ld, zinv, det, tau, status, cnt, s);
     case kCompF64:
-      return dispatch_stat<kCompF64>(z, n, ld, zinv, det, tau, status, cnt, s, di);
-    case kChol: return dispatch_stat<kChol>(z, n, ld, zinv, det, tau, status, cnt, s, di);
+      return dispatch_stat<kCompF64>(z, n, ld, zinv, det, tau, status, cnt, s);
+    case kChol: return dispatch_stat<kChol>(z, n, ld, zinv, det, tau, status, cnt, s);
   }
   return ZINV_ERR_ARG;
 }
