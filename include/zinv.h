@@ -235,7 +235,7 @@ int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int64_t W, int
  * Same arguments and results as wishart_stat_fwd without ws and ws_bytes; the
  * caller still passes the inputs and outputs.  The per-tile partial sums go to
  * a fixed 1 MiB device array inside libzinv.so, held by every GPU that loads the
- * library until the process exits.  Maximum size: ceil(W/64) * ceil(H/8) <=
+ * library until the process exits.  Maximum size: ceil(W/32) * ceil(H/16) <=
  * 131072 tiles (e.g. 8192 x 8192 pixels); larger images return ZINV_ERR_ARG.
  * The call allocates no device memory.  Its first call on a device looks up the
  * array's device address for that device; make that first call before any

@@ -22,6 +22,7 @@
 // Each input row is loaded once per strip (plus 2r rows at a segment start and
 // 2r halo columns): ~1.1x the ideal read traffic.  The weighted window uses a
 // simpler tiled kernel.
+#include "async.cuh"
 #include "common.cuh"
 #include "pixel.cuh"
 
@@ -180,22 +181,6 @@ struct Strip {
   static constexpr size_t ring_f = 9 * RING * kTW;
   static constexpr size_t smem = kStages * stage_f2 * sizeof(float2) + ring_f * sizeof(float);
 };
-
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 // Issues the asynchronous copies of `rows` input rows (relative rows rr0 ..,
 // absolute y_begin - R + rr, clamped) of the three planes, columns x0-4 ..

@@ -34,19 +34,6 @@ struct NlmArgs {
   float* out;
 };
 
-// det of the 3x3 Hermitian matrix in packed form x by Algorithm 2's first-column
-// cofactor expansion.
-__device__ __forceinline__ float det_adjugate(const float x[9]) {
-  const float a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
-  const float d = x[5], er = x[6], ei = x[7], f = x[8];
-  const float ac = d * f - (er * er + ei * ei);
-  const float bcr = (cr * er + ci * ei) - br * f;
-  const float bci = (ci * er - cr * ei) - bi * f;
-  const float ccr = (br * er - bi * ei) - cr * d;
-  const float cci = (br * ei + bi * er) - ci * d;
-  return a * ac + br * bcr + bi * bci + cr * ccr + ci * cci;
-}
-
 // det by Algorithm 1's factorization: (l00 l11 l22)^2 with l00 = sqrt(a), the
 // first column scaled by 1/l00, l11 = sqrt(d - |l10|^2), l21 scaled by 1/l11,
 // l22 = sqrt(f - |l20|^2 - |l21|^2) (correctly rounded sqrt and reciprocal).

@@ -171,6 +171,24 @@ __device__ __forceinline__ dd<T> det_comp(const T x[9]) {
   return out;
 }
 
+// det alone by Alg. 2's first-column cofactor expansion (the a_c, b_c, c_c of
+// Eq. adjoint_elements in Eq. detr), plain FP32.
+__device__ __forceinline__ float det_adjugate(const float x[9]) {
+  const float a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
+  const float d = x[5], er = x[6], ei = x[7], f = x[8];
+  const float ac = d * f - (er * er + ei * ei);
+  const float bcr = (cr * er + ci * ei) - br * f;
+  const float bci = (ci * er - cr * ei) - bi * f;
+  const float ccr = (br * er - bi * ei) - cr * d;
+  const float cci = (br * ei + bi * er) - ci * d;
+  return a * ac + br * bcr + bi * bci + cr * ccr + ci * cci;
+}
+
+// ln det, from hi + lo: ln(hi) + ln(1 + lo/hi) with |lo/hi| <= 2^-24.
+__device__ __forceinline__ float log_dd(const dd<float>& d) {
+  return logf(d.hi) + __fdividef(d.lo, d.hi);
+}
+
 // ---------------------------------------------------------------------------
 // Alg. 1 (§2.2), Cholesky route, FP32 with correctly rounded sqrt and
 // reciprocal.  Z = L L^H, L lower triangular with real positive diagonal:

@@ -11,15 +11,21 @@
 //             = sum_p sum_t sum_c G_t[c](p) P_t[c](p+k),
 // with P the nine channel products of S S^H and G the packed form of M (off-
 // diagonal entries doubled).  Determinants and inverses use the compensated
-// route of Algorithm 2 (Dot2), so the log-dets keep FP32 accuracy.
+// route of Algorithm 2 (Dot2), so the log-dets keep FP32 accuracy: on scenes
+// with strongly correlated channels det / (a d f) falls to a few 10^-3, where
+// the plain expansion loses most of its digits.
 //
-// Tiles of 64 x 8 outputs, 128 threads, each thread four adjacent outputs of one
-// row.  One date's channel products for the tile and its halo sit in shared
-// memory at a time, staged from values each thread prefetched into registers
-// while the previous stage was being used; a thread slides over a product row
-// with 128-bit loads, 28 FMAs per loaded row, one channel at a time.  Each tile writes its partial sums (FP64) to the workspace; a
-// one-block-per-output kernel adds them in tile order.  No float atomics: the
-// results are the same bits on every run.
+// Tiles of 32 x 16 outputs, 64 threads, each thread a block of 4 x 2 outputs.
+// One date's channel products for the tile and its halo sit in shared memory
+// at a time, staged from values each thread prefetched into registers while
+// the previous stage was being used.  A thread slides down a product column
+// with 128-bit loads: each of the win + 1 input rows it loads feeds both of its
+// output rows (2 x 4 x win FMAs per loaded row), one channel at a time.  In the
+// forward, the second date's Z replaces its own products channel by channel,
+// so a CTA needs ~50 KB and four fit on an SM.  Each tile writes its partial
+// sums (FP64) to the workspace; a one-block-per-output kernel adds them in
+// tile order.  No float atomics: the results are the same bits on every run.
+#include "async.cuh"
 #include "common.cuh"
 #include "pixel.cuh"
 
@@ -27,10 +33,12 @@ namespace zinv {
 
 namespace {
 
-constexpr int kWT = 128;  // threads per CTA
-constexpr int kTW = 64;   // tile width (outputs)
-constexpr int kTH = 8;    // tile height (outputs)
+constexpr int kWT = 64;       // threads per CTA (two warps)
+constexpr int kTW = 32;       // tile width (outputs)
+constexpr int kTH = 16;       // tile height (outputs)
+constexpr int kTX = kTW / 4;  // threads across a tile row (4 outputs each)
 constexpr int kRedThreads = 256;
+static_assert(kTX * (kTH / 2) == kWT, "each thread owns a 4 x 2 block of outputs");
 
 struct WsArgs {
   const float2* s[2];
@@ -42,13 +50,20 @@ struct WsArgs {
 
 template <int R>
 struct WTile {
+  static constexpr int L = 2 * R + 1;
+  static constexpr int K = L * L;
   static constexpr int SH = kTH + 2 * R;
   static constexpr int SW = kTW + 2 * R;
   static constexpr int SWP = (SW + 3) / 4 * 4;
-  static constexpr int NV = (4 + 2 * R + 3) / 4;              // float4 loads per row segment
-  static constexpr int KO = (SH * SW + kWT - 1) / kWT;       // staged pixels per thread
-  static constexpr int P_FLOATS = 9 * SH * SWP;              // one date's products
-  static constexpr int Z_FLOATS = 2 * 9 * kTH * kTW;         // Z (then G) of both dates
+  static constexpr int NV = (4 + 2 * R + 3) / 4;            // float4 loads per row segment
+  static constexpr int KO = (SH * SW + kWT - 1) / kWT;     // staged pixels per thread
+  static constexpr int PLANE = SH * SWP;                   // one channel's products
+  static constexpr int P_FLOATS = 9 * PLANE;               // one date's products
+  static constexpr int Z_FLOATS = 9 * kTH * kTW;           // one date's Z
+  static_assert(P_FLOATS >= Z_FLOATS, "a date's Z fits in place of its products");
+  static constexpr int WROW = 8;                           // tap rows padded for 128-bit loads
+  static constexpr int S_F2 = 3 * SH * SW;                 // one date's single-look block (float2)
+  static_assert((P_FLOATS + Z_FLOATS) % 4 == 0 && S_F2 % 2 == 0, "16-byte aligned regions");
 };
 
 __device__ __forceinline__ int64_t clampi(int64_t v, int64_t hi) {
@@ -106,7 +121,7 @@ __device__ __forceinline__ void store_products(const float2 (&v)[WTile<R>::KO][3
       float p[9];
       products(v[k][0], v[k][1], v[k][2], p);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) P[(c * T::SH + r) * T::SWP + x] = p[c];
+      for (int c = 0; c < 9; ++c) P[c * T::PLANE + r * T::SWP + x] = p[c];
     }
     x += dx;
     r += dr;
@@ -118,13 +133,11 @@ __device__ __forceinline__ void store_products(const float2 (&v)[WTile<R>::KO][3
 }
 
 template <int R>
-__device__ __forceinline__ void load_row(const float* P, int c, int iy, int x0,
-                                         float row[4 * WTile<R>::NV]) {
-  using T = WTile<R>;
-  const float4* src = reinterpret_cast<const float4*>(P + (c * T::SH + iy) * T::SWP + x0);
+__device__ __forceinline__ void load_row(const float* src, float (&row)[4 * WTile<R>::NV]) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
-  for (int q = 0; q < T::NV; ++q) {
-    const float4 v = src[q];
+  for (int q = 0; q < WTile<R>::NV; ++q) {
+    const float4 v = s4[q];
     row[4 * q] = v.x;
     row[4 * q + 1] = v.y;
     row[4 * q + 2] = v.z;
@@ -132,34 +145,147 @@ __device__ __forceinline__ void load_row(const float* P, int c, int iy, int x0,
   }
 }
 
-// Z_t of the thread's four outputs (tile row y, columns x0..x0+3), one channel
-// at a time (a runtime loop: small code), into Zb[t][c][y][x0..x0+3].
 template <int R>
-__device__ __forceinline__ void window_cov(const float* P, const float* wsh, int t, int y,
-                                           int x0, float* Zb) {
-  constexpr int L = 2 * R + 1;
-#pragma unroll 1
-  for (int c = 0; c < 9; ++c) {
-    float z[4] = {0.f, 0.f, 0.f, 0.f};
+__device__ __forceinline__ void load_weights(const float* weights, float (&w)[WTile<R>::K]) {
 #pragma unroll
-    for (int dy = 0; dy < L; ++dy) {
-      float row[4 * WTile<R>::NV];
-      load_row<R>(P, c, y + dy, x0, row);
+  for (int k = 0; k < WTile<R>::K; ++k) w[k] = __ldg(weights + k);
+}
+
+// One channel's window sums for the thread's 4 x 2 outputs (tile rows y0 and
+// y0 + 1, columns x0..x0+3) from that channel's staged products Pc [SH][SWP].
+// Each of the L + 1 input rows is loaded once and feeds both output rows; per
+// output the taps are added in row-major order.
+template <int R>
+__device__ __forceinline__ void window_4x2(const float* Pc, const float (&w)[WTile<R>::K], int y0,
+                                           int x0, float (&z)[2][4]) {
+  using T = WTile<R>;
+  constexpr int L = T::L;
 #pragma unroll
-      for (int dx = 0; dx < L; ++dx) {
-        const float wk = wsh[dy * L + dx];
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) z[i] = fmaf(wk, row[i + dx], z[i]);
-      }
+    for (int i = 0; i < 4; ++i) z[r][i] = 0.0f;
+#pragma unroll
+  for (int iy = 0; iy <= L; ++iy) {
+    float row[4 * T::NV];
+    load_row<R>(Pc + (y0 + iy) * T::SWP + x0, row);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int dy = iy - r;
+      if (dy < 0 || dy >= L) continue;
+#pragma unroll
+      for (int dx = 0; dx < L; ++dx)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) z[r][i] = fmaf(w[dy * L + dx], row[i + dx], z[r][i]);
     }
-    *reinterpret_cast<float4*>(Zb + ((t * 9 + c) * kTH + y) * kTW + x0) =
-        make_float4(z[0], z[1], z[2], z[3]);
   }
 }
 
-__device__ __forceinline__ float log_dd(const dd<float>& d) {
-  // ln(hi + lo) = ln(hi) + ln(1 + lo/hi), |lo/hi| <= 2^-24
-  return logf(d.hi) + d.lo / d.hi;
+// One input row of all nine channels for the thread's 4 x 2 outputs: the row
+// y0 + iy feeds output row 0 with tap row iy (ROW0) and output row 1 with tap
+// row iy - 1 (ROW1).  Taps come from the shared table wsh [L][WROW].
+template <int R, bool ROW0, bool ROW1>
+__device__ __forceinline__ void row_step(const float* P, const float* wsh, int iy, int y0,
+                                         int x0, float (&z)[9][2][4]) {
+  using T = WTile<R>;
+  constexpr int L = T::L;
+  float w0[2 * 4], w1[2 * 4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (ROW0) {
+      const float4 q = *reinterpret_cast<const float4*>(wsh + iy * T::WROW + 4 * h);
+      w0[4 * h] = q.x, w0[4 * h + 1] = q.y, w0[4 * h + 2] = q.z, w0[4 * h + 3] = q.w;
+    }
+    if (ROW1) {
+      const float4 q = *reinterpret_cast<const float4*>(wsh + (iy - 1) * T::WROW + 4 * h);
+      w1[4 * h] = q.x, w1[4 * h + 1] = q.y, w1[4 * h + 2] = q.z, w1[4 * h + 3] = q.w;
+    }
+  }
+  const float* src = P + (y0 + iy) * T::SWP + x0;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    float row[4 * T::NV];
+    load_row<R>(src + c * T::PLANE, row);
+#pragma unroll
+    for (int dx = 0; dx < L; ++dx)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (ROW0) z[c][0][i] = fmaf(w0[dx], row[i + dx], z[c][0][i]);
+        if (ROW1) z[c][1][i] = fmaf(w1[dx], row[i + dx], z[c][1][i]);
+      }
+  }
+}
+
+// Window sums of all nine channels for the thread's 4 x 2 outputs from one
+// date's staged products P: the L + 1 input rows in order, the first and last
+// feeding one output row each.  Per output the taps are added in row-major
+// order, as in window_4x2.
+template <int R>
+__device__ __forceinline__ void window_all(const float* P, const float* wsh, int y0, int x0,
+                                           float (&z)[9][2][4]) {
+  constexpr int L = WTile<R>::L;
+#pragma unroll
+  for (int c = 0; c < 9; ++c)
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) z[c][r][i] = 0.0f;
+  row_step<R, true, false>(P, wsh, 0, y0, x0, z);
+#pragma unroll 1
+  for (int iy = 1; iy < L; ++iy) row_step<R, true, true>(P, wsh, iy, y0, x0, z);
+  row_step<R, false, true>(P, wsh, L, y0, x0, z);
+}
+
+// Copies the taps into the shared table [L][WROW] (pad entries unused).
+template <int R>
+__device__ __forceinline__ void stage_taps(const float* weights, float* wsh) {
+  using T = WTile<R>;
+  for (int k = threadIdx.x; k < T::K; k += kWT) wsh[(k / T::L) * T::WROW + k % T::L] = weights[k];
+}
+
+// Issues, as one cp.async group, the copies of date t's single-look block of a
+// tile plus halo (clamp-to-edge) into Sb [3][SH][SW].
+template <int R>
+__device__ __forceinline__ void issue_block(const WsArgs& a, int t, int64_t tile, float2* Sb) {
+  using T = WTile<R>;
+  const int64_t tiles_x = (a.W + kTW - 1) / kTW;
+  const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
+  for (int i = threadIdx.x; i < T::SH * T::SW; i += kWT) {
+    const int r = i / T::SW, x = i - r * T::SW;
+    const int64_t q = clampi(ty0 - R + r, a.H - 1) * a.W + clampi(tx0 - R + x, a.W - 1);
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+      cp_async8(Sb + p * T::SH * T::SW + i, a.s[t] + p * a.plane_ld + q);
+  }
+  cp_async_commit();
+}
+
+// The nine channel products of the staged block Sb -> P[c][SH][SWP].
+template <int R>
+__device__ __forceinline__ void block_products(const float2* Sb, float* P) {
+  using T = WTile<R>;
+  for (int i = threadIdx.x; i < T::SH * T::SW; i += kWT) {
+    const int r = i / T::SW, x = i - r * T::SW;
+    float p[9];
+    products(Sb[i], Sb[T::SH * T::SW + i], Sb[2 * T::SH * T::SW + i], p);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) P[c * T::PLANE + r * T::SWP + x] = p[c];
+  }
+}
+
+// Stages date t's products of a tile (plus halo) into P with direct loads.
+template <int R>
+__device__ __forceinline__ void stage(const WsArgs& a, int t, int64_t tile, float* P) {
+  float2 v[WTile<R>::KO][3];
+  prefetch<R>(a, t, tile, v);
+  store_products<R>(v, P);
+}
+
+// Stores the thread's 4 x 2 block of one channel into a [kTH][kTW] plane.
+__device__ __forceinline__ void store_block(float* Zc, int y0, int x0, const float (&z)[2][4]) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+    *reinterpret_cast<float4*>(Zc + (y0 + r) * kTW + x0) =
+        make_float4(z[r][0], z[r][1], z[r][2], z[r][3]);
 }
 
 // Fixed-order block reduction of one double per thread; returns the sum in thread 0.
@@ -179,44 +305,51 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 template <int R>
 __global__ void __launch_bounds__(kWT, 3) k_wishart_fwd(WsArgs a) {
   using T = WTile<R>;
-  constexpr int L = 2 * R + 1;
   extern __shared__ __align__(16) float smem[];
-  float* P = smem;
-  float* Zb = smem + T::P_FLOATS;
-  float* wsh = Zb + T::Z_FLOATS;
-  double* red = reinterpret_cast<double*>(wsh + 64);
-  for (int i = threadIdx.x; i < L * L; i += blockDim.x) wsh[i] = a.weights[i];
+  float* P = smem;                    // one date's products [9][SH][SWP]; then date 2's Z
+  float* Z0 = smem + T::P_FLOATS;     // date 1's Z [9][kTH][kTW]
+  float2* Sb = reinterpret_cast<float2*>(Z0 + T::Z_FLOATS);  // next single-look block
+  float* wsh = reinterpret_cast<float*>(Sb + T::S_F2);       // taps [L][WROW]
+  double* red = reinterpret_cast<double*>(wsh + T::L * T::WROW);
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
-  const int y = threadIdx.x / (kTW / 4), x0 = (threadIdx.x % (kTW / 4)) * 4;
+  const int y0 = 2 * (threadIdx.x / kTX), x0 = 4 * (threadIdx.x % kTX);
   const float six_ln2 = 4.15888308335967185650f;
-  float2 v[T::KO][3];
-  if ((int64_t)blockIdx.x < tiles) prefetch<R>(a, 0, blockIdx.x, v);
+  stage_taps<R>(a.weights, wsh);
+  if ((int64_t)blockIdx.x < tiles) issue_block<R>(a, 0, blockIdx.x, Sb);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
+    float* Z1 = P;  // date 2's Z [9][kTH][kTW], over its products once all are read
 #pragma unroll 1
     for (int t = 0; t < 2; ++t) {
-      __syncthreads();  // everyone is done reading P
-      store_products<R>(v, P);
-      if (t == 0)
-        prefetch<R>(a, 1, tile, v);
-      else if (tile + gridDim.x < tiles)
-        prefetch<R>(a, 0, tile + gridDim.x, v);
-      __syncthreads();
-      window_cov<R>(P, wsh, t, y, x0, Zb);
+      cp_async_wait<0>();
+      __syncthreads();  // date t's block is in Sb; P is free (and the taps are in place)
+      block_products<R>(Sb, P);
+      __syncthreads();  // Sb is free; P holds date t's products
+      // the next block (date 2 of this tile, then date 1 of the next) loads
+      // while this date's window sums run
+      const int64_t next = t == 0 ? tile : tile + gridDim.x;
+      if (next < tiles) issue_block<R>(a, 1 - t, next, Sb);
+      float z[9][2][4];
+      window_all<R>(P, wsh, y0, x0, z);
+      if (t == 1) __syncthreads();
+      float* dst = t == 0 ? Z0 : Z1;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) store_block(dst + c * kTH * kTW, y0, x0, z[c]);
     }
-    // per output: compensated log-dets of Z1, Z2 and Z1 + Z2 (own Zb entries only)
+    __syncthreads();
+    // per output: compensated log-dets of Z1, Z2 and Z1 + Z2.  Output o =
+    // tid + kWT j (row o / kTW): a warp reads one row's 32 entries of a plane.
     double qsum = 0.0;
-    const int64_t gy = ty0 + y;
 #pragma unroll 1
-    for (int i = 0; i < 4; ++i) {
-      const int64_t gx = tx0 + x0 + i;
+    for (int o = threadIdx.x; o < kTH * kTW; o += kWT) {
+      const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
       if (gy >= a.H || gx >= a.W) continue;
       float z1[9], z2[9], z12[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        z1[c] = Zb[((0 * 9 + c) * kTH + y) * kTW + x0 + i];
-        z2[c] = Zb[((1 * 9 + c) * kTH + y) * kTW + x0 + i];
+        z1[c] = Z0[c * kTH * kTW + o];
+        z2[c] = Z1[c * kTH * kTW + o];
         z12[c] = z1[c] + z2[c];
       }
       const float l1 = log_dd(det_comp<float>(z1));
@@ -229,103 +362,117 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_fwd(WsArgs a) {
     const double s = block_sum(qsum, red);
     if (threadIdx.x == 0) a.partial[tile] = s;
   }
+  cp_async_wait<0>();
 }
 
 template <int R>
 __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
   using T = WTile<R>;
-  constexpr int L = 2 * R + 1;
-  constexpr int K = L * L;
+  constexpr int L = T::L;
+  constexpr int K = T::K;
   extern __shared__ __align__(16) float smem[];
   float* P = smem;
   float* G = smem + T::P_FLOATS;  // [2][9][kTH][kTW]: Z_t, then the packed M_t
-  float* wsh = G + T::Z_FLOATS;
-  double* red = reinterpret_cast<double*>(wsh + 64);  // [4 warps][K]
-  for (int i = threadIdx.x; i < K; i += blockDim.x) wsh[i] = a.weights[i];
+  double* red = reinterpret_cast<double*>(G + 2 * T::Z_FLOATS);  // [kWT / 32][K]
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
-  const int y = threadIdx.x / (kTW / 4), x0 = (threadIdx.x % (kTW / 4)) * 4;
-  float2 v[T::KO][3];
-  // P holds one date at a time.  Per tile: stage date 0 (Z_0), stage date 1
-  // (Z_1, then its correlation while still staged), stage date 0 again (its
-  // correlation).  Each stage's loads were issued during the previous stage.
-  if ((int64_t)blockIdx.x < tiles) prefetch<R>(a, 0, blockIdx.x, v);
+  const int y0 = 2 * (threadIdx.x / kTX), x0 = 4 * (threadIdx.x % kTX);
+  // P holds one date at a time.  Per tile, three stages: date 1 (its Z), date 2
+  // (its Z, the inverses, then its correlation while still staged), date 1
+  // again (its correlation).  Staging loads directly (no register prefetch:
+  // the registers go to the 49 tap accumulators; the other CTAs on the SM
+  // cover the load latency).
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
-    // Z_0 and Z_1
-#pragma unroll 1
-    for (int t = 0; t < 2; ++t) {
-      __syncthreads();
-      store_products<R>(v, P);
-      if (t == 0) prefetch<R>(a, 1, tile, v);
-      else prefetch<R>(a, 0, tile, v);  // date 0 again, for its correlation
-      __syncthreads();
-      window_cov<R>(P, wsh, t, y, x0, G);
-    }
-    // per output: three compensated inverses, M_t = W_t - 2 W_12 in packed
-    // gradient form written over the thread's own Z slots
-    {
-      const int64_t gy = ty0 + y;
-#pragma unroll 1
-      for (int i = 0; i < 4; ++i) {
-        const int64_t gx = tx0 + x0 + i;
-        float z1[9], z2[9], z12[9], w1[9], w2[9], w12[9], d;
-#pragma unroll
-        for (int c = 0; c < 9; ++c) {
-          z1[c] = G[((0 * 9 + c) * kTH + y) * kTW + x0 + i];
-          z2[c] = G[((1 * 9 + c) * kTH + y) * kTW + x0 + i];
-          z12[c] = z1[c] + z2[c];
-        }
-        const bool inside = gy < a.H && gx < a.W;
-        adjugate_inv_det_comp<float>(z1, w1, d);
-        adjugate_inv_det_comp<float>(z2, w2, d);
-        adjugate_inv_det_comp<float>(z12, w12, d);
-#pragma unroll
-        for (int c = 0; c < 9; ++c) {
-          // packed M_t = W_t - 2 W_12; off-diagonal packed reals count twice
-          const float two = (c == 0 || c == 5 || c == 8) ? 1.0f : 2.0f;
-          G[((0 * 9 + c) * kTH + y) * kTW + x0 + i] = inside ? two * fmaf(-2.0f, w12[c], w1[c]) : 0.0f;
-          G[((1 * 9 + c) * kTH + y) * kTW + x0 + i] = inside ? two * fmaf(-2.0f, w12[c], w2[c]) : 0.0f;
-        }
-      }
-    }
-    // dL/dw_k over this thread's four pixels: sum_t sum_c G_t[c](p) P_t[c](p + k);
-    // P still holds date 1: correlate it first, then stage date 0.
     float acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0f;
 #pragma unroll 1
-    for (int step = 0; step < 2; ++step) {
-      const int t = 1 - step;
-      if (step == 1) {
+    for (int phase = 0; phase < 3; ++phase) {
+      const int t = phase == 1 ? 1 : 0;  // the date staged now
+      __syncthreads();
+      stage<R>(a, t, tile, P);
+      __syncthreads();
+      if (phase < 2) {
+        float w[K];
+        load_weights<R>(a.weights, w);
+#pragma unroll 1
+        for (int c = 0; c < 9; ++c) {
+          float z[2][4];
+          window_4x2<R>(P + c * T::PLANE, w, y0, x0, z);
+          store_block(G + (t * 9 + c) * kTH * kTW, y0, x0, z);
+        }
+      }
+      if (phase == 1) {
+        // per output: three compensated inverses, M_t = W_t - 2 W_12 in packed
+        // gradient form over the Z slots.  Output o = tid + kWT j, so a warp
+        // reads one row's 32 entries of a plane.
         __syncthreads();
-        store_products<R>(v, P);
-        if (tile + gridDim.x < tiles) prefetch<R>(a, 0, tile + gridDim.x, v);
+#pragma unroll 1
+        for (int o = threadIdx.x; o < kTH * kTW; o += kWT) {
+          const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
+          float z1[9], z2[9], z12[9], w1[9], w2[9], w12[9], d;
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            z1[c] = G[c * kTH * kTW + o];
+            z2[c] = G[(9 + c) * kTH * kTW + o];
+            z12[c] = z1[c] + z2[c];
+          }
+          const bool inside = gy < a.H && gx < a.W;
+          adjugate_inv_det_comp<float>(z1, w1, d);
+          adjugate_inv_det_comp<float>(z2, w2, d);
+          adjugate_inv_det_comp<float>(z12, w12, d);
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            // packed M_t = W_t - 2 W_12; off-diagonal packed reals count twice
+            const float two = (c == 0 || c == 5 || c == 8) ? 1.0f : 2.0f;
+            G[c * kTH * kTW + o] = inside ? two * fmaf(-2.0f, w12[c], w1[c]) : 0.0f;
+            G[(9 + c) * kTH * kTW + o] = inside ? two * fmaf(-2.0f, w12[c], w2[c]) : 0.0f;
+          }
+        }
         __syncthreads();
       }
+      if (phase > 0) {
+        // dL/dw_k over the thread's 4 x 2 pixels: sum_c G_t[c](p) P_t[c](p + k)
 #pragma unroll 1
-      for (int c = 0; c < 9; ++c) {
-        const float4 gv = *reinterpret_cast<const float4*>(G + ((t * 9 + c) * kTH + y) * kTW + x0);
-        const float gi[4] = {gv.x, gv.y, gv.z, gv.w};
+        for (int c = 0; c < 9; ++c) {
+          const float* Gc = G + (t * 9 + c) * kTH * kTW;
+          float g[2][4];
 #pragma unroll
-        for (int dy = 0; dy < L; ++dy) {
-          float row[4 * WTile<R>::NV];
-          load_row<R>(P, c, y + dy, x0, row);
+          for (int r = 0; r < 2; ++r) {
+            const float4 gv = *reinterpret_cast<const float4*>(Gc + (y0 + r) * kTW + x0);
+            g[r][0] = gv.x;
+            g[r][1] = gv.y;
+            g[r][2] = gv.z;
+            g[r][3] = gv.w;
+          }
+          const float* Pc = P + c * T::PLANE;
 #pragma unroll
-          for (int dx = 0; dx < L; ++dx)
+          for (int iy = 0; iy <= L; ++iy) {
+            float row[4 * T::NV];
+            load_row<R>(Pc + (y0 + iy) * T::SWP + x0, row);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[dy * L + dx] = fmaf(gi[i], row[i + dx], acc[dy * L + dx]);
+            for (int r = 0; r < 2; ++r) {
+              const int dy = iy - r;
+              if (dy < 0 || dy >= L) continue;
+#pragma unroll
+              for (int dx = 0; dx < L; ++dx)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                  acc[dy * L + dx] = fmaf(g[r][i], row[i + dx], acc[dy * L + dx]);
+            }
+          }
         }
       }
     }
     // fixed-order reduction of the K taps over the block
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double vsum = (double)acc[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) vsum += __shfl_down_sync(0xffffffffu, vsum, o);
-      if (lane == 0) red[warp * K + k] = vsum;
+      if (lane_id == 0) red[warp * K + k] = vsum;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -358,12 +505,14 @@ __global__ void __launch_bounds__(kRedThreads)
 
 template <int R>
 size_t fwd_smem() {
-  return (WTile<R>::P_FLOATS + WTile<R>::Z_FLOATS + 64) * sizeof(float) + 8 * sizeof(double);
+  using T = WTile<R>;
+  return (T::P_FLOATS + T::Z_FLOATS + T::L * T::WROW) * sizeof(float) +
+         T::S_F2 * sizeof(float2) + (kWT / 32) * sizeof(double);
 }
 template <int R>
 size_t bwd_smem() {
-  constexpr int K = (2 * R + 1) * (2 * R + 1);
-  return (WTile<R>::P_FLOATS + WTile<R>::Z_FLOATS + 64) * sizeof(float) + 4 * K * sizeof(double);
+  using T = WTile<R>;
+  return (T::P_FLOATS + 2 * T::Z_FLOATS) * sizeof(float) + (kWT / 32) * T::K * sizeof(double);
 }
 
 int64_t tile_count(int64_t H, int64_t W) {
@@ -475,7 +624,7 @@ extern "C" int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int
 // ---------------------------------------------------------------------------
 namespace zinv {
 namespace {
-constexpr int64_t kNoAllocTiles = 131072;  // one slot per 64 x 8 tile: 8192 x 8192 pixels
+constexpr int64_t kNoAllocTiles = 131072;  // one slot per 32 x 16 tile: 8192 x 8192 pixels
 __device__ __align__(256) double g_noalloc_partials[kNoAllocTiles];
 
 struct NoAllocScratch {

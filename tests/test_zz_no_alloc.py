@@ -61,7 +61,7 @@ def test_noalloc_rejects_images_beyond_its_scratch(zlib):
     wts = torch.full((49,), 1 / 49, device="cuda")
     loss = torch.zeros((), dtype=torch.float64, device="cuda")
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    # 8200 x 8192 needs 1025 x 128 tiles > 131072: refused before any device work
+    # 8200 x 8192 needs 513 x 256 tiles > 131072: refused before any device work
     H, W = 8200, 8192
     assert f(s.data_ptr(), s.data_ptr(), H, W, H * W, 7, wts.data_ptr(), None, loss.data_ptr(),
              stream) == -1
