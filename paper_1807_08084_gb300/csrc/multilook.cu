@@ -6,7 +6,7 @@
 // Algorithm 2 (same per-pixel code and flags as zinv_det).  Z never reaches HBM:
 // 24 B are read and 40 B written per pixel.
 //
-// Boxcar: persistent CTAs walk strip segments (kTW columns x kSeg rows) down
+// Boxcar: each CTA walks one strip segment (kTW columns x kSeg rows) down
 // the image in steps of kCH output rows.  Per step:
 //   - cp.async copies of the step's raw input rows (three planes, the r-column
 //     halo, clamp-to-edge rows; 16-byte copies inside the image, clamped 8-byte
