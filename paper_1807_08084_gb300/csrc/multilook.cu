@@ -171,12 +171,19 @@ constexpr int kCH = 8;       // output rows per step
 constexpr int kSeg = 256;    // rows per strip segment
 constexpr int kStages = 3;   // raw-row buffers in flight
 constexpr int kRawW = kTW + 8;  // raw columns x0-4 .. x0+67 (covers r <= 4), 16-byte aligned
+// Row stride of the raw buffers, in float2: one 16-byte unit more than the
+// copied columns, so consecutive rows start one bank group apart (37 units,
+// odd).  Phase H gives a half-warp 8 column groups of two rows, and the 16
+// lanes' 8-byte reads of input k then fall into 8 distinct bank groups (2-way
+// instead of 4-way conflicts).
+constexpr int kRawS = kRawW + 2;
+static_assert(kCH % 2 == 0, "phase H pairs rows");
 
 template <int R>
 struct Strip {
   static_assert(R <= 4, "raw rows cover a halo of at most 4");
   static constexpr int RING = kCH + 2 * R;                      // rows of horizontal sums
-  static constexpr size_t stage_f2 = 3 * kCH * kRawW;           // float2 per raw buffer
+  static constexpr size_t stage_f2 = 3 * kCH * kRawS;           // float2 per raw buffer
   // horizontal sums: float2 [4][RING][kTW] (channel pairs) then float [RING][kTW]
   static constexpr size_t ring_f = 9 * RING * kTW;
   static constexpr size_t smem = kStages * stage_f2 * sizeof(float2) + ring_f * sizeof(float);
@@ -197,7 +204,7 @@ __device__ __forceinline__ void issue_rows_t(const MlArgs& a, float2* buf, int64
     const int p = pr / ROWS, r = pr - p * ROWS;
     const int64_t gy = clamp64(y_begin - R + rr0 + r, a.H - 1);
     const float2* row = a.s + p * a.plane_ld + gy * a.W;
-    float2* dst = buf + (p * kCH + r) * kRawW;
+    float2* dst = buf + (p * kCH + r) * kRawS;
     if (VEC16)
       cp_async16(dst + 2 * ch, row + (x0 - 4) + 2 * ch);
     else
@@ -261,15 +268,18 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
       // phase H: products of 4 + 2R pixels and horizontal sums of four adjacent
       // outputs per work item, rows of this job -> ring
       for (int i = threadIdx.x; i < rows * (kTW / 4); i += kSThreads) {
-        const int r = i / (kTW / 4), xr = (i % (kTW / 4)) * 4;
+        // items in groups of 16: rows 2 (g / 2) and 2 (g / 2) + 1, column
+        // groups 8 (g % 2) .. + 7 (rows is even: kCH or 2R)
+        const int g = i >> 4, sub = i & 15;
+        const int r = 2 * (g >> 1) + (sub >> 3), xr = 4 * (8 * (g & 1) + (sub & 7));
         const int cbase = xr + 4 - R;  // raw column of the run's first input
         float2 pv2[4][4 + 2 * R];
         float pv8[4 + 2 * R];
 #pragma unroll
         for (int k = 0; k < 4 + 2 * R; ++k) {
-          const float2 s0 = rb[(0 * kCH + r) * kRawW + cbase + k];
-          const float2 s1 = rb[(1 * kCH + r) * kRawW + cbase + k];
-          const float2 s2 = rb[(2 * kCH + r) * kRawW + cbase + k];
+          const float2 s0 = rb[(0 * kCH + r) * kRawS + cbase + k];
+          const float2 s1 = rb[(1 * kCH + r) * kRawS + cbase + k];
+          const float2 s2 = rb[(2 * kCH + r) * kRawS + cbase + k];
           float pp[9];
           channels(s0, s1, s2, pp);
           pv2[0][k] = make_float2(pp[0], pp[5]);

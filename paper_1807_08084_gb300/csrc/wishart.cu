@@ -63,7 +63,8 @@ struct WTile {
   static_assert(P_FLOATS >= Z_FLOATS, "a date's Z fits in place of its products");
   static constexpr int WROW = 8;                           // tap rows padded for 128-bit loads
   static constexpr int S_F2 = 3 * SH * SW;                 // one date's single-look block (float2)
-  static_assert((P_FLOATS + Z_FLOATS) % 4 == 0 && S_F2 % 2 == 0, "16-byte aligned regions");
+  static_assert(P_FLOATS % 4 == 0 && S_F2 % 2 == 0, "16-byte aligned regions");
+  static_assert(P_FLOATS >= 2 * 9 * (kTH / 2) * kTW, "half a tile's Z of both dates fits in P");
 };
 
 __device__ __forceinline__ int64_t clampi(int64_t v, int64_t hi) {
@@ -303,23 +304,25 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kWT, 3) k_wishart_fwd(WsArgs a) {
+__global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
   using T = WTile<R>;
   extern __shared__ __align__(16) float smem[];
-  float* P = smem;                    // one date's products [9][SH][SWP]; then date 2's Z
-  float* Z0 = smem + T::P_FLOATS;     // date 1's Z [9][kTH][kTW]
-  float2* Sb = reinterpret_cast<float2*>(Z0 + T::Z_FLOATS);  // next single-look block
-  float* wsh = reinterpret_cast<float*>(Sb + T::S_F2);       // taps [L][WROW]
+  float* P = smem;  // one date's products [9][SH][SWP]; then Z of half a tile [2][9][kTH/2][kTW]
+  float2* Sb = reinterpret_cast<float2*>(smem + T::P_FLOATS);  // next single-look block
+  float* wsh = reinterpret_cast<float*>(Sb + T::S_F2);         // taps [L][WROW]
   double* red = reinterpret_cast<double*>(wsh + T::L * T::WROW);
+  constexpr int HALF = kTH / 2 * kTW;  // outputs in half a tile (one warp's rows)
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
   const int y0 = 2 * (threadIdx.x / kTX), x0 = 4 * (threadIdx.x % kTX);
+  const int warp = threadIdx.x >> 5;  // warp w owns tile rows 8w .. 8w + 7
   const float six_ln2 = 4.15888308335967185650f;
   stage_taps<R>(a.weights, wsh);
   if ((int64_t)blockIdx.x < tiles) issue_block<R>(a, 0, blockIdx.x, Sb);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
-    float* Z1 = P;  // date 2's Z [9][kTH][kTW], over its products once all are read
+    float z0[9][2][4];  // date 1's Z of the thread's 4 x 2 outputs
+    double qsum = 0.0;
 #pragma unroll 1
     for (int t = 0; t < 2; ++t) {
       cp_async_wait<0>();
@@ -332,32 +335,49 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_fwd(WsArgs a) {
       if (next < tiles) issue_block<R>(a, 1 - t, next, Sb);
       float z[9][2][4];
       window_all<R>(P, wsh, y0, x0, z);
-      if (t == 1) __syncthreads();
-      float* dst = t == 0 ? Z0 : Z1;
+      if (t == 0) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) store_block(dst + c * kTH * kTW, y0, x0, z[c]);
-    }
-    __syncthreads();
-    // per output: compensated log-dets of Z1, Z2 and Z1 + Z2.  Output o =
-    // tid + kWT j (row o / kTW): a warp reads one row's 32 entries of a plane.
-    double qsum = 0.0;
-#pragma unroll 1
-    for (int o = threadIdx.x; o < kTH * kTW; o += kWT) {
-      const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
-      if (gy >= a.H || gx >= a.W) continue;
-      float z1[9], z2[9], z12[9];
+        for (int c = 0; c < 9; ++c)
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        z1[c] = Z0[c * kTH * kTW + o];
-        z2[c] = Z1[c * kTH * kTW + o];
-        z12[c] = z1[c] + z2[c];
+          for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) z0[c][r][i] = z[c][r][i];
+        continue;
       }
-      const float l1 = log_dd(det_comp<float>(z1));
-      const float l2 = log_dd(det_comp<float>(z2));
-      const float l12 = log_dd(det_comp<float>(z12));
-      const float q = (l1 + l2) - 2.0f * l12 + six_ln2;
-      if (a.q_map) a.q_map[gy * a.W + gx] = q;
-      qsum += (double)q;
+      // Both dates' Z are in registers.  Per half tile (one warp's rows): that
+      // warp writes them over the products, then all threads take the
+      // compensated log-dets of Z1, Z2 and Z1 + Z2 of its 256 outputs
+      // (output o: row o / kTW, so a warp reads one row's 32 entries of a plane).
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        __syncthreads();  // P is free: products read (h = 0), half 0 done (h = 1)
+        if (warp == h) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            store_block(P + c * HALF, y0 - 8 * h, x0, z0[c]);
+            store_block(P + (9 + c) * HALF, y0 - 8 * h, x0, z[c]);
+          }
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int o = threadIdx.x; o < HALF; o += kWT) {
+          const int64_t gy = ty0 + 8 * h + o / kTW, gx = tx0 + o % kTW;
+          if (gy >= a.H || gx >= a.W) continue;
+          float z1[9], z2[9], z12[9];
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            z1[c] = P[c * HALF + o];
+            z2[c] = P[(9 + c) * HALF + o];
+            z12[c] = z1[c] + z2[c];
+          }
+          const float l1 = log_dd(det_comp<float>(z1));
+          const float l2 = log_dd(det_comp<float>(z2));
+          const float l12 = log_dd(det_comp<float>(z12));
+          const float q = (l1 + l2) - 2.0f * l12 + six_ln2;
+          if (a.q_map) a.q_map[gy * a.W + gx] = q;
+          qsum += (double)q;
+        }
+      }
     }
     const double s = block_sum(qsum, red);
     if (threadIdx.x == 0) a.partial[tile] = s;
@@ -506,8 +526,8 @@ __global__ void __launch_bounds__(kRedThreads)
 template <int R>
 size_t fwd_smem() {
   using T = WTile<R>;
-  return (T::P_FLOATS + T::Z_FLOATS + T::L * T::WROW) * sizeof(float) +
-         T::S_F2 * sizeof(float2) + (kWT / 32) * sizeof(double);
+  return (T::P_FLOATS + T::L * T::WROW) * sizeof(float) + T::S_F2 * sizeof(float2) +
+         (kWT / 32) * sizeof(double);
 }
 template <int R>
 size_t bwd_smem() {
