@@ -24,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -179,6 +180,41 @@ def timed(fn, steps: int, warmup: int, world: int) -> float:
     return max_over_ranks(e0.elapsed_time(e1) / steps, world)
 
 
+def timed_stats(fn, steps: int, warmup: int, world: int) -> dict:
+    """As timed(), plus the fastest and the median single call: an event is
+    recorded between consecutive calls (max over ranks of each statistic)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    s = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(s)
+    for i in range(steps):
+        fn()
+        ev[i + 1].record(s)
+    torch.cuda.synchronize()
+    barrier(world)
+    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(steps))
+    return {"mean": max_over_ranks(ev[0].elapsed_time(ev[steps]) / steps, world),
+            "min": max_over_ranks(per[0], world),
+            "median": max_over_ranks(per[steps // 2], world)}
+
+
+def host_cpu() -> str:
+    """CPU model and core count of this host, as the OS reports them."""
+    model = platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return f"{model}, {os.cpu_count()} cores"
+
+
 def cpu_oracle_baseline(z_dev: torch.Tensor, budget_s: float = 12.0):
     """The FP64 oracle on the host cores, on the first pixels of the same image,
     chunk after chunk until ~budget_s of oracle time."""
@@ -195,6 +231,7 @@ def cpu_oracle_baseline(z_dev: torch.Tensor, budget_s: float = 12.0):
         done += zc.shape[1]
         p0 += chunk
     return {"value": done / spent / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": f"first {done} matrices of the same image, FP64 Gauss-Jordan "
                       f"inverse and det, single thread ({spent:.1f} s)"}
 
@@ -223,7 +260,7 @@ def run_reference(args, world, rank):
             "config": {"workload": f"{w.name}: first {m} of 16384x16384 packed Z, N=16 looks, "
                                    "8 classes in 512x512 blocks (bounded CPU sample)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{m} matrices per step"},
+                             "host": host_cpu(), "sample": f"{m} matrices per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -249,13 +286,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    world, rank, local = dist_setup(args)
     if args.impl == "reference":
-        run_reference(args, world, rank)
-        if world > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
+        # host-only: rank 0 times the oracle, the other ranks exit without work
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")),
+                      int(os.environ.get("RANK", "0")))
         return
+    world, rank, local = dist_setup(args)
 
     import paper_1807_08084_gb300 as zp
     from paper_1807_08084_gb300 import synth as S
@@ -291,8 +327,13 @@ def main():
 
     paths = {"adjugate": path(ms)}
     sub = args.sub_steps
-    paths["cholesky"] = path(timed(lambda: zp.chol_zinv_det(z, out=(zinv, det)), sub,
-                                   args.warmup, world))
+    # single-launch statistics of the two routes (events between launches)
+    st_adj = timed_stats(lambda: zp.zinv_det(z, zp.PLAIN, out=(zinv, det)), sub, args.warmup,
+                         world)
+    st_chol = timed_stats(lambda: zp.chol_zinv_det(z, out=(zinv, det)), sub, args.warmup, world)
+    paths["adjugate"].update({"ms_min": st_adj["min"], "ms_median": st_adj["median"]})
+    paths["cholesky"] = path(st_chol["mean"])
+    paths["cholesky"].update({"ms_min": st_chol["min"], "ms_median": st_chol["median"]})
     paths["compensated"] = path(timed(lambda: zp.zinv_det(z, zp.COMPENSATED, out=(zinv, det)),
                                       sub, args.warmup, world))
     counts = zp.zinv_det(z, zp.FP64_RECOMPUTE, want_counts=True, out=(zinv, det))[2]
