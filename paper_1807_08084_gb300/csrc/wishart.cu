@@ -15,16 +15,22 @@
 // with strongly correlated channels det / (a d f) falls to a few 10^-3, where
 // the plain expansion loses most of its digits.
 //
-// Tiles of 32 x 16 outputs, 64 threads, each thread a block of 4 x 2 outputs.
-// One date's channel products for the tile and its halo sit in shared memory
-// at a time, staged from values each thread prefetched into registers while
-// the previous stage was being used.  A thread slides down a product column
-// with 128-bit loads: each of the win + 1 input rows it loads feeds both of its
-// output rows (2 x 4 x win FMAs per loaded row), one channel at a time.  In the
-// forward, the second date's Z replaces its own products channel by channel,
-// so a CTA needs ~50 KB and four fit on an SM.  Each tile writes its partial
-// sums (FP64) to the workspace; a one-block-per-output kernel adds them in
-// tile order.  No float atomics: the results are the same bits on every run.
+// Tiles of 32 x 16 outputs, 64 threads, each thread a block of 4 x 2 outputs,
+// so each input row a thread loads from shared memory feeds both of its output
+// rows (2 x 4 x win FMAs per loaded row).  One date's channel products for the
+// tile and its halo sit in shared memory at a time.
+//   Forward: each date's single-look block is copied with cp.async while the
+//   other date's window sums run; the window is summed with the input rows as
+//   the outer loop and the nine channels unrolled (Z in registers); date 1's Z
+//   stays in registers while date 2's is summed, then both are written over
+//   the products half a tile at a time for the log-dets: ~52 KB per CTA, four
+//   CTAs per SM.
+//   Backward: blocks are loaded directly; the window is summed one channel at a
+//   time (the registers go to the 49 tap accumulators); Z, then the packed
+//   M_t, are parked in shared memory for the correlations.
+// Each tile writes its partial sums (FP64) to the workspace; a one-block-per-
+// output kernel adds them in tile order.  No float atomics: the results are the
+// same bits on every run.
 #include "async.cuh"
 #include "common.cuh"
 #include "pixel.cuh"
