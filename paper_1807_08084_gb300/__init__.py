@@ -385,6 +385,11 @@ def zinv_det_host(z_host: torch.Tensor, ws: torch.Tensor | None = None, flags: i
         det = torch.empty(z_host.shape[1:], dtype=torch.float32, pin_memory=True)
     else:
         zinv, det = out
+        if (zinv.is_cuda or zinv.dtype != torch.float32 or zinv.shape != z_host.shape
+                or not zinv.is_contiguous()):
+            raise ValueError("zinv must be a contiguous float32 host tensor shaped like z_host")
+        if det.is_cuda or det.dtype != torch.float32 or det.numel() != n or not det.is_contiguous():
+            raise ValueError(f"det must be a contiguous float32 host tensor of {n} elements")
     dev = (ws.device if ws is not None else torch.device("cuda", torch.cuda.current_device())) \
         if device is None else device
     with torch.cuda.device(dev):

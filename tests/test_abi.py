@@ -74,3 +74,23 @@ def test_host_argument_checks():
                              None) == -1  # workspace not 256-byte aligned
     assert lib.zinv_det_host_workspace_bytes(0) == 0
     assert lib.zinv_det_host_workspace_bytes(1024) >= 3 * 40 * 1024
+
+
+def test_binding_rejects_bad_tensors():
+    """The Python binding refuses CPU tensors for device entry points and
+    mis-shaped host outputs before the library is called."""
+    import torch
+    import paper_1807_08084_gb300 as zp
+    z = torch.zeros(9, 8)
+    with pytest.raises(ValueError):
+        zp.zinv_det(z)                       # there is no CPU path
+    with pytest.raises(ValueError):
+        zp.chol_zinv_det(z)
+    bad = torch.zeros(9, 7)                  # one pixel short
+    det = torch.zeros(8)
+    with pytest.raises(ValueError):
+        zp.zinv_det_host(z, out=(bad, det))
+    with pytest.raises(ValueError):
+        zp.zinv_det_host(z, out=(torch.zeros(9, 8), torch.zeros(7)))
+    with pytest.raises(ValueError):
+        zp.zinv_det_host(z, out=(torch.zeros(9, 8, dtype=torch.float64), det))
