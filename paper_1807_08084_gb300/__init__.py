@@ -125,6 +125,23 @@ def _planes(z: torch.Tensor, name: str = "z", nplanes: int = 9):
     return n, n
 
 
+def _like(t: torch.Tensor, ref: torch.Tensor, name: str, ref_name: str):
+    """t must be a float32 tensor with ref's device, shape and strides."""
+    if (t.dtype != torch.float32 or t.device != ref.device or t.shape != ref.shape
+            or t.stride() != ref.stride()):
+        raise ValueError(f"{name} must be float32 with the device, shape and strides of {ref_name}")
+    return t
+
+
+def _out(t: torch.Tensor, shape, device, name: str):
+    """A caller-supplied output: contiguous float32 of `shape` on `device`."""
+    if (t.dtype != torch.float32 or t.device != device or tuple(t.shape) != tuple(shape)
+            or not t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 tensor of shape {tuple(shape)} "
+                         f"on {device}")
+    return t
+
+
 def _flat(x: torch.Tensor | None, n: int, name: str):
     if x is None:
         return None
@@ -154,8 +171,7 @@ def _inv_det(fn, z, flags, tau, want_status, want_counts, out):
         det = torch.empty(z.shape[1:], dtype=torch.float32, device=z.device)
     else:
         zinv, det = out
-        if zinv.shape != z.shape or zinv.stride() != z.stride() or zinv.device != z.device:
-            raise ValueError("zinv must have the shape and strides of z")
+        _like(zinv, z, "zinv", "z")
         _flat(det, n, "det")
     status = torch.empty(z.shape[1:], dtype=torch.uint8, device=z.device) if want_status else None
     counts = torch.empty(2, dtype=torch.int64, device=z.device) if want_counts else None
@@ -178,16 +194,13 @@ def zinv_det_bwd(zinv: torch.Tensor, det: torch.Tensor, g_zinv=None, g_det=None,
     n, ld = _planes(zinv, "zinv")
     _flat(det, n, "det")
     if g_zinv is not None:
-        if g_zinv.shape != zinv.shape or g_zinv.stride() != zinv.stride():
-            raise ValueError("g_zinv must match zinv")
+        _like(g_zinv, zinv, "g_zinv", "zinv")
     _flat(g_det, n, "g_det")
     _flat(g_logdet, n, "g_logdet")
     if out is None:
         g_z = torch.empty_strided(zinv.shape, zinv.stride(), dtype=zinv.dtype, device=zinv.device)
     else:
-        g_z = out
-        if g_z.shape != zinv.shape or g_z.stride() != zinv.stride():
-            raise ValueError("out must have the shape and strides of zinv")
+        g_z = _like(out, zinv, "out", "zinv")
     with torch.cuda.device(zinv.device):
         rc = lib.zinv_det_bwd(_ptr(zinv), _ptr(det), n, ld, _ptr(g_zinv), _ptr(g_det),
                               _ptr(g_logdet), _ptr(g_z), _stream(zinv.device))
@@ -224,7 +237,8 @@ def multilook_zinv_det(s: torch.Tensor, win: int = 7, weights: torch.Tensor | No
         zinv = torch.empty((9, H, W), dtype=torch.float32, device=s.device)
         det = torch.empty((H, W), dtype=torch.float32, device=s.device)
     else:
-        zinv, det = out
+        zinv = _out(out[0], (9, H, W), s.device, "zinv")
+        det = _out(out[1], (H, W), s.device, "det")
     status = torch.empty((H, W), dtype=torch.uint8, device=s.device) if want_status else None
     counts = torch.empty(2, dtype=torch.int64, device=s.device) if want_counts else None
     with torch.cuda.device(s.device):
@@ -284,6 +298,8 @@ def nlm_wishart(z: torch.Tensor, radius: int = 11, looks: float = 16.0, h: float
     H, W = z.shape[1], z.shape[2]
     if out is None:
         out = torch.empty((9, H, W), dtype=torch.float32, device=z.device)
+    else:
+        _out(out, (9, H, W), z.device, "out")
     with torch.cuda.device(z.device):
         rc = lib.nlm_wishart(_ptr(z), H, W, ld, int(radius), float(looks), float(h), int(method),
                              _ptr(out), _stream(z.device))

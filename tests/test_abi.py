@@ -94,3 +94,22 @@ def test_binding_rejects_bad_tensors():
         zp.zinv_det_host(z, out=(torch.zeros(9, 8), torch.zeros(7)))
     with pytest.raises(ValueError):
         zp.zinv_det_host(z, out=(torch.zeros(9, 8, dtype=torch.float64), det))
+
+
+def test_binding_rejects_mismatched_outputs():
+    """Caller-supplied outputs and gradients of the wrong dtype or shape are
+    refused in Python (a smaller buffer would otherwise be overrun)."""
+    import torch
+    import paper_1807_08084_gb300 as zp
+    z = torch.zeros(9, 8)
+    with pytest.raises(ValueError):
+        zp._like(torch.zeros(9, 8, dtype=torch.float16), z, "out", "z")
+    with pytest.raises(ValueError):
+        zp._like(torch.zeros(9, 4), z, "out", "z")
+    with pytest.raises(ValueError):
+        zp._like(torch.zeros(8, 9).t(), z, "out", "z")     # same shape, other strides
+    assert zp._like(torch.zeros(9, 8), z, "out", "z").shape == z.shape
+    with pytest.raises(ValueError):
+        zp._out(torch.zeros(9, 4, 4, dtype=torch.float64), (9, 4, 4), z.device, "out")
+    with pytest.raises(ValueError):
+        zp._out(torch.zeros(9, 4, 5), (9, 4, 4), z.device, "out")
