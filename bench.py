@@ -279,6 +279,8 @@ def main():
     ap.add_argument("--wishart", type=int, default=1, help="also time the Wishart statistic")
     ap.add_argument("--nlm", type=int, default=1, help="also time the nonlocal-means filter")
     ap.add_argument("--blockdiag", type=int, default=1, help="also time 3-band block-diagonal pixels")
+    ap.add_argument("--precision", type=int, default=1,
+                    help="also time the precision modes on the cond-controlled workload")
     ap.add_argument("--nlm-rows", type=int, default=1024, help="nonlocal-means image side")
     ap.add_argument("--ws-rows", type=int, default=4096, help="Wishart image height")
     ap.add_argument("--rows", type=int, default=16384,
@@ -392,6 +394,27 @@ def main():
                      "workload": "8192x8192 pixels x 3 bands of packed Z (scale_16k generator)"}
         del zb
 
+    # --- precision modes where the FP64 recompute has work: the cond-controlled
+    # 4096 x 4096 workload (cond log-uniform in [1, 1e7]) ----------------------
+    precision = {}
+    if args.precision:
+        wp = S.WORKLOADS["precision_4k"]
+        zp4 = G.packed_z(wp)
+        zi4 = torch.empty_like(zp4)
+        d4 = torch.empty((wp.H, wp.W), device="cuda")
+        for name, flags in (("plain", zp.PLAIN), ("compensated", zp.COMPENSATED),
+                            ("plain_fp64", zp.FP64_RECOMPUTE),
+                            ("compensated_fp64", zp.COMPENSATED | zp.FP64_RECOMPUTE)):
+            t = timed(lambda: zp.zinv_det(zp4, flags, out=(zi4, d4)), sub, args.warmup, world)
+            gbs = BYTES_FWD * wp.n / (t * 1e-3) / 1e9
+            precision[name] = {"ms": t, "gmat_s": wp.n / (t * 1e-3) / 1e9, "gbs": gbs,
+                               "frac_hbm": gbs / hbm_peak}
+        cnt = zp.zinv_det(zp4, zp.FP64_RECOMPUTE, want_counts=True, out=(zi4, d4))[2]
+        precision["flagged_fraction"] = int(cnt[1]) / wp.n
+        precision["workload"] = ("4096x4096 packed Z = U diag(1, k^-v, 1/k) U^H, k log-uniform "
+                                 "in [1, 1e7], tau = 2^-10")
+        del zp4, zi4, d4
+
     # --- nonlocal means, 23 x 23 search window: arithmetic-bound per-pair dets --
     nlm = {}
     if args.nlm:
@@ -486,6 +509,7 @@ def main():
             "wishart_pair_4k": wishart or None,
             "nlm_23x23": nlm or None,
             "blockdiag_3band": blockdiag or None,
+            "precision_4k": precision or None,
             "speedup_vs_cholesky": paths["cholesky"]["ms"] / ms,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_scalar(BwdArgs a) {
 }
 
 template <bool HG, bool HD, bool HL>
-int launch_bwd(const BwdArgs& a, cudaStream_t s) {
+int launch_bwd(const BwdArgs& a, cudaStream_t s, int64_t min_blocks) {
   const bool vec = (a.ld % 4 == 0) && aligned(a.w, 16) && aligned(a.det, 16) &&
                    aligned(a.g, 16) && aligned(a.gd, 16) && aligned(a.gl, 16) &&
                    aligned(a.out, 16);
@@ -154,7 +154,8 @@ int launch_bwd(const BwdArgs& a, cudaStream_t s) {
     const int64_t items = (a.n >> 2) > 0 ? (a.n >> 2) : 1;
     // With g_W given the kernel holds 128 registers (two blocks per SM); 32
     // groups per thread streamed 3.5% faster there than one (GB300 sweep).
-    k<<<(unsigned)cover_blocks(items, kBwdThreads, HG ? 32 : 1), kBwdThreads, 0, s>>>(a);
+    k<<<(unsigned)cover_blocks(items, kBwdThreads, HG ? 32 : 1, min_blocks), kBwdThreads, 0,
+        s>>>(a);
   } else {
     auto k = k_bwd_scalar<HG, HD, HL>;
     k<<<(unsigned)cover_blocks(a.n, kBwdThreads), kBwdThreads, 0, s>>>(a);
@@ -183,14 +184,15 @@ extern "C" int zinv_det_bwd(const float* zinv, const float* det, int64_t n, int6
   BwdArgs a{zinv, det, g_zinv, g_det, g_logdet, g_z, n, ld};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int key = (g_zinv ? 4 : 0) | (g_det ? 2 : 0) | (g_logdet ? 1 : 0);
+  const int64_t mb = (int64_t)kMinBlocksPerSm * di.sm_count;
   switch (key) {
-    case 0: return launch_bwd<false, false, false>(a, s);
-    case 1: return launch_bwd<false, false, true>(a, s);
-    case 2: return launch_bwd<false, true, false>(a, s);
-    case 3: return launch_bwd<false, true, true>(a, s);
-    case 4: return launch_bwd<true, false, false>(a, s);
-    case 5: return launch_bwd<true, false, true>(a, s);
-    case 6: return launch_bwd<true, true, false>(a, s);
-    default: return launch_bwd<true, true, true>(a, s);
+    case 0: return launch_bwd<false, false, false>(a, s, mb);
+    case 1: return launch_bwd<false, false, true>(a, s, mb);
+    case 2: return launch_bwd<false, true, false>(a, s, mb);
+    case 3: return launch_bwd<false, true, true>(a, s, mb);
+    case 4: return launch_bwd<true, false, false>(a, s, mb);
+    case 5: return launch_bwd<true, false, true>(a, s, mb);
+    case 6: return launch_bwd<true, true, false>(a, s, mb);
+    default: return launch_bwd<true, true, true>(a, s, mb);
   }
 }

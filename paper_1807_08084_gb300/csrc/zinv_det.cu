@@ -116,12 +116,13 @@ __global__ void __launch_bounds__(kThreads)
 template <int ALG, bool STAT>
 static int launch_inv_det(const float* z, int64_t n, int64_t ld, float* zinv, float* det,
                           float tau, uint8_t* status, unsigned long long* counts,
-                          cudaStream_t s) {
+                          cudaStream_t s, int64_t min_blocks) {
   const bool vec = (ld % 4 == 0) && aligned(z, 16) && aligned(zinv, 16) && aligned(det, 16) &&
                    (status == nullptr || aligned(status, 4));
   if (vec) {
     const int64_t items = (n >> 2) > 0 ? (n >> 2) : 1;
-    const unsigned blocks = (unsigned)cover_blocks(items, kThreads, kGroupsPerThread<ALG>);
+    const unsigned blocks =
+        (unsigned)cover_blocks(items, kThreads, kGroupsPerThread<ALG>, min_blocks);
     if constexpr (ALG == kCompF64)
       k_inv_det_vec4_c64<STAT><<<blocks, kThreads, 0, s>>>(z, n, ld, zinv, det, tau, status,
                                                            counts);
@@ -138,10 +139,11 @@ static int launch_inv_det(const float* z, int64_t n, int64_t ld, float* zinv, fl
 
 template <int ALG>
 static int dispatch_stat(const float* z, int64_t n, int64_t ld, float* zinv, float* det,
-                         float tau, uint8_t* status, unsigned long long* counts, cudaStream_t s) {
+                         float tau, uint8_t* status, unsigned long long* counts, cudaStream_t s,
+                         int64_t min_blocks) {
   if (status || counts)
-    return launch_inv_det<ALG, true>(z, n, ld, zinv, det, tau, status, counts, s);
-  return launch_inv_det<ALG, false>(z, n, ld, zinv, det, tau, status, counts, s);
+    return launch_inv_det<ALG, true>(z, n, ld, zinv, det, tau, status, counts, s, min_blocks);
+  return launch_inv_det<ALG, false>(z, n, ld, zinv, det, tau, status, counts, s, min_blocks);
 }
 
 // Shared argument checks of zinv_det / chol_zinv_det: sizes and pointer
@@ -178,14 +180,15 @@ int inv_det_entry(int alg, const float* z, int64_t n, int64_t ld, float* zinv, f
   if (cnt && cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
     return ZINV_ERR_LAUNCH;
   if (n == 0) return ZINV_OK;
+  const int64_t mb = (int64_t)kMinBlocksPerSm * di.sm_count;
   switch (alg) {
-    case kPlain: return dispatch_stat<kPlain>(z, n, ld, zinv, det, tau, status, cnt, s);
-    case kComp: return dispatch_stat<kComp>(z, n, ld, zinv, det, tau, status, cnt, s);
+    case kPlain: return dispatch_stat<kPlain>(z, n, ld, zinv, det, tau, status, cnt, s, mb);
+    case kComp: return dispatch_stat<kComp>(z, n, ld, zinv, det, tau, status, cnt, s, mb);
     case kPlainF64:
-      return dispatch_stat<kPlainF64>(z, n, ld, zinv, det, tau, status, cnt, s);
+      return dispatch_stat<kPlainF64>(z, n, ld, zinv, det, tau, status, cnt, s, mb);
     case kCompF64:
-      return dispatch_stat<kCompF64>(z, n, ld, zinv, det, tau, status, cnt, s);
-    case kChol: return dispatch_stat<kChol>(z, n, ld, zinv, det, tau, status, cnt, s);
+      return dispatch_stat<kCompF64>(z, n, ld, zinv, det, tau, status, cnt, s, mb);
+    case kChol: return dispatch_stat<kChol>(z, n, ld, zinv, det, tau, status, cnt, s, mb);
   }
   return ZINV_ERR_ARG;
 }
