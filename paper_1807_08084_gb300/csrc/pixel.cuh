@@ -238,9 +238,45 @@ __device__ __forceinline__ void cholesky_inv_det(const float x[9], float w[9], f
 }
 
 // ---------------------------------------------------------------------------
+// Flagged-pixel recompute (not in the paper; it follows its stability
+// discussion in §3.3).  Hadamard's inequality gives det/(a d f) in (0, 1] for
+// positive definite Z; a small ratio means cancellation ate the FP32 digits.
+// !(>) also catches NaN and det <= 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool needs_recompute(float det, const float x[9], float tau) {
+  return !(det > tau * (x[0] * x[5] * x[8]));
+}
+
+// The compensated route in FP64 on the FP32 inputs: their products and the
+// Dot2 sums are exact enough that only the final FP32 rounding remains, even
+// where the plain FP64 route would lose u64*cond^2.  Returns the pixel's status
+// bits (RECOMPUTED, and NOT_PD from the FP64 det).
+__device__ __forceinline__ uint32_t recompute_f64(const float x[9], float w[9], float& det) {
+  double xd[9], wd[9], det64;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) xd[k] = (double)x[k];
+  adjugate_inv_det_comp<double>(xd, wd, det64);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) w[k] = __double2float_rn(wd[k]);
+  det = __double2float_rn(det64);
+  uint32_t st = ZINV_PIX_RECOMPUTED;
+  if (!(det64 > 0.0) || !isfinite(det64)) st |= ZINV_PIX_NOT_PD;
+  return st;
+}
+
+// ---------------------------------------------------------------------------
 // Dispatch over the algorithm variants; returns the pixel's ZINV_PIX_* bits.
+// The FP64 variants recompute a flagged pixel inline here (one-pixel paths);
+// the four-pixel kernel queues them instead (zinv_det.cu).
 // ---------------------------------------------------------------------------
 enum Alg : int { kPlain = 0, kComp = 1, kPlainF64 = 2, kCompF64 = 3, kChol = 4 };
+
+// The FP32 route an algorithm variant starts from.
+template <int ALG>
+constexpr int kBaseAlg = ALG == kPlainF64 ? kPlain : (ALG == kCompF64 ? kComp : ALG);
+
+template <int ALG>
+constexpr bool kHasF64 = ALG == kPlainF64 || ALG == kCompF64;
 
 template <int ALG>
 __device__ __forceinline__ uint32_t pixel_inv_det(const float x[9], float w[9], float& det,
@@ -252,28 +288,8 @@ __device__ __forceinline__ uint32_t pixel_inv_det(const float x[9], float w[9], 
   } else {
     adjugate_inv_det<float>(x, w, det);
   }
-  uint32_t st = 0;
-  if (ALG == kPlainF64 || ALG == kCompF64) {
-    // Hadamard ratio det/(a d f) in (0, 1] for positive definite Z; a small
-    // ratio means cancellation ate the FP32 digits.  !(>) also catches NaN.
-    // The recompute is the compensated route in FP64: products of FP32 inputs
-    // and their Dot2 sums are exact enough that only the final FP32 rounding
-    // remains, even where the plain FP64 route would lose u64*cond^2.
-    if (!(det > tau * (x[0] * x[5] * x[8]))) {
-      double xd[9], wd[9], det64;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) xd[k] = (double)x[k];
-      adjugate_inv_det_comp<double>(xd, wd, det64);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) w[k] = __double2float_rn(wd[k]);
-      det = __double2float_rn(det64);
-      st |= ZINV_PIX_RECOMPUTED;
-      if (!(det64 > 0.0) || !isfinite(det64)) st |= ZINV_PIX_NOT_PD;
-      return st;
-    }
-  }
-  if (!(det > 0.0f) || !isfinite(det)) st |= ZINV_PIX_NOT_PD;
-  return st;
+  if (kHasF64<ALG> && needs_recompute(det, x, tau)) return recompute_f64(x, w, det);
+  return (!(det > 0.0f) || !isfinite(det)) ? ZINV_PIX_NOT_PD : 0u;
 }
 
 // float4 lane access with a compile-time lane after unrolling

@@ -9,6 +9,13 @@
 // image (see kGroupsPerThread for the per-variant split), which streamed
 // faster than a persistent grid.  Pixels that do not fill a float4 (n % 4) and
 // unaligned layouts take the one-pixel-per-thread kernel, still coalesced.
+//
+// FP64 recompute variants: the four-pixel kernel takes every pixel through
+// the FP32 route and stores it; each warp queues its flagged pixels in shared
+// memory and recomputes them 32 at a time, one per lane, overwriting the FP32
+// results.  FP64 runs at 1/64 of the FP32 rate on GB300, so a warp that took
+// the FP64 branch for whichever of its lanes were flagged (about half of them
+// on an ill-conditioned scene) spent most of its time on idle lanes.
 #include "common.cuh"
 #include "pixel.cuh"
 
@@ -16,14 +23,22 @@ namespace zinv {
 
 constexpr int kThreads = 256;
 
-// Launch shape per variant, from a sweep on GB300 over a 16384 x 16384 image.
+// Launch shape per variant, from sweeps on GB300 over the 16384 x 16384 image
+// (nothing flagged) and the 4096 x 4096 cond-controlled one (54% flagged).
 // The light variants stream best with one group of four pixels per thread.
-// The compensated ones hold more registers and arithmetic per group and run
-// best with several groups per thread: 32 for compensated (3.21 -> 3.02 ms),
-// 16 for compensated + FP64, whose register cap for three blocks per SM (at
-// the cost of some spills) took it from 4.22 to 3.43 ms.
+// The compensated one holds more registers and arithmetic per group and runs
+// best with 32 groups per thread (3.21 -> 3.02 ms).  The FP64 variants take
+// 16 (plain) and 32 (compensated) groups, so a warp's queue fills whole rounds
+// of 32 and a partial round runs once per thread's share: on the ill-
+// conditioned image 7.66 ms with one group, 6.04 with 16, for 2% more on the
+// image where nothing is flagged.
 template <int ALG>
-constexpr int kGroupsPerThread = ALG == kComp ? 32 : ALG == kCompF64 ? 16 : 1;
+constexpr int kGroupsPerThread =
+    ALG == kComp ? 32 : ALG == kCompF64 ? 32 : ALG == kPlainF64 ? 16 : 1;
+
+// Per-warp queue of flagged pixels: at most 31 left from the last flush plus
+// 128 from one step (four pixels per lane).
+constexpr int kQueue = 160;
 
 template <int ALG, bool STAT>
 __device__ __forceinline__ void one_pixel(const float* __restrict__ z, int64_t ld, int64_t p,
@@ -84,6 +99,119 @@ __device__ __forceinline__ void inv_det_vec4(const float* __restrict__ z, int64_
   if (STAT && counts) add_counts(counts, c0, c1);
 }
 
+// Recomputes queued pixel p in FP64.  Its owning lane parked the input in the
+// pixel's zinv slots (so zinv == z, in place, works too), ordered before this
+// by a __syncwarp; the FP64 results overwrite it.
+template <bool STAT>
+__device__ __forceinline__ void recompute_queued(int64_t ld, int64_t p, float* zinv,
+                                                 float* __restrict__ det,
+                                                 uint8_t* __restrict__ status, uint32_t& c0) {
+  float x[9], w[9], dt;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) x[k] = __ldcg(zinv + k * ld + p);
+  const uint32_t st = recompute_f64(x, w, dt);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) __stcs(zinv + k * ld + p, w[k]);
+  __stcs(det + p, dt);
+  if (STAT) {
+    if (status) status[p] = (uint8_t)st;
+    c0 += st & ZINV_PIX_NOT_PD;
+  }
+}
+
+// Recomputes the warp's queued pixels in whole rounds of 32, from the end of
+// the queue; returns how many are left (< 32).  (Out of line it ran 3-4%
+// slower on images with nothing flagged: the call's register saves.)
+template <bool STAT>
+__device__ __forceinline__ int flush_rounds(const int64_t* q, int qn, int ln, int64_t ld,
+                                         float* zinv, float* det, uint8_t* status,
+                                         uint32_t& c0) {
+  __syncwarp();  // queue entries and the FP32 stores are visible to the warp
+  do {
+    qn -= 32;
+    recompute_queued<STAT>(ld, q[qn + ln], zinv, det, status, c0);
+  } while (qn >= 32);
+  __syncwarp();  // the queue slots are read before the next step refills them
+  return qn;
+}
+
+// Four-pixel kernel of the FP64 variants.  The loop is warp-uniform (lanes
+// past the last group idle through a step), so ballots and __syncwarp see the
+// whole warp.  For a flagged pixel the owning lane stores its input in place
+// of the inverse and status RECOMPUTED; the lane that recomputes it stores the
+// FP64 results, the status byte (with NOT_PD from the FP64 det) and counts
+// NOT_PD.
+template <int ALG, bool STAT>
+__device__ __forceinline__ void inv_det_vec4_queued(const float* __restrict__ z, int64_t n,
+                                                    int64_t ld, float* __restrict__ zinv,
+                                                    float* __restrict__ det, float tau,
+                                                    uint8_t* __restrict__ status,
+                                                    unsigned long long* __restrict__ counts) {
+  constexpr int BASE = kBaseAlg<ALG>;
+  __shared__ int64_t queue[kThreads / 32][kQueue];
+  int64_t* q = queue[threadIdx.x >> 5];
+  const int ln = threadIdx.x & 31;
+  const unsigned below = (1u << ln) - 1u;
+  int qn = 0;  // warp-uniform
+  const int64_t groups = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t c0 = 0, c1 = 0;
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); g0 < groups;
+       g0 += stride) {
+    const int64_t g = g0 + ln;
+    uint32_t flags = 0;  // bit j: pixel 4g + j waits for the FP64 recompute
+    if (g < groups) {
+      float4 v[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) v[k] = __ldcs(reinterpret_cast<const float4*>(z + k * ld) + g);
+      float4 o[9], dv;
+      uint32_t sv = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float x[9], w[9], dt;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) x[k] = lane(v[k], j);
+        uint32_t st = pixel_inv_det<BASE>(x, w, dt, tau);
+        if (needs_recompute(dt, x, tau)) {
+          flags |= 1u << j;
+          st = ZINV_PIX_RECOMPUTED;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) w[k] = x[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) set_lane(o[k], j, w[k]);
+        set_lane(dv, j, dt);
+        if (STAT) {
+          sv |= st << (8 * j);
+          c0 += st & ZINV_PIX_NOT_PD;
+          c1 += (st & ZINV_PIX_RECOMPUTED) >> 1;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) __stcs(reinterpret_cast<float4*>(zinv + k * ld) + g, o[k]);
+      __stcs(reinterpret_cast<float4*>(det) + g, dv);
+      if (STAT && status) reinterpret_cast<uint32_t*>(status)[g] = sv;
+    }
+    if (__any_sync(0xffffffffu, flags != 0u)) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const unsigned m = __ballot_sync(0xffffffffu, (flags >> j) & 1u);
+        if ((flags >> j) & 1u) q[qn + __popc(m & below)] = 4 * g + j;
+        qn += __popc(m);
+      }
+      if (qn >= 32) qn = flush_rounds<STAT>(q, qn, ln, ld, zinv, det, status, c0);
+    }
+  }
+  if (qn > 0) {
+    __syncwarp();
+    if (ln < qn) recompute_queued<STAT>(ld, q[ln], zinv, det, status, c0);
+  }
+  // ragged tail: n % 4 pixels after the last full group, recomputed inline
+  const int64_t p = (groups << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && p < n) one_pixel<ALG, STAT>(z, ld, p, zinv, det, tau, status, c0, c1);
+  if (STAT && counts) add_counts(counts, c0, c1);
+}
+
 template <int ALG, bool STAT>
 __global__ void __launch_bounds__(kThreads)
     k_inv_det_vec4(const float* __restrict__ z, int64_t n, int64_t ld, float* __restrict__ zinv,
@@ -92,13 +220,14 @@ __global__ void __launch_bounds__(kThreads)
   inv_det_vec4<ALG, STAT>(z, n, ld, zinv, det, tau, status, counts);
 }
 
-// Compensated + FP64 recompute, held to three blocks per SM.
-template <bool STAT>
+// FP64 recompute variants, held to three blocks per SM (their FP64 code would
+// otherwise cost the FP32 streaming pass a block).
+template <int ALG, bool STAT>
 __global__ void __launch_bounds__(kThreads, 3)
-    k_inv_det_vec4_c64(const float* __restrict__ z, int64_t n, int64_t ld,
+    k_inv_det_vec4_f64(const float* __restrict__ z, int64_t n, int64_t ld,
                        float* __restrict__ zinv, float* __restrict__ det, float tau,
                        uint8_t* __restrict__ status, unsigned long long* __restrict__ counts) {
-  inv_det_vec4<kCompF64, STAT>(z, n, ld, zinv, det, tau, status, counts);
+  inv_det_vec4_queued<ALG, STAT>(z, n, ld, zinv, det, tau, status, counts);
 }
 
 template <int ALG, bool STAT>
@@ -123,9 +252,9 @@ static int launch_inv_det(const float* z, int64_t n, int64_t ld, float* zinv, fl
     const int64_t items = (n >> 2) > 0 ? (n >> 2) : 1;
     const unsigned blocks =
         (unsigned)cover_blocks(items, kThreads, kGroupsPerThread<ALG>, min_blocks);
-    if constexpr (ALG == kCompF64)
-      k_inv_det_vec4_c64<STAT><<<blocks, kThreads, 0, s>>>(z, n, ld, zinv, det, tau, status,
-                                                           counts);
+    if constexpr (kHasF64<ALG>)
+      k_inv_det_vec4_f64<ALG, STAT><<<blocks, kThreads, 0, s>>>(z, n, ld, zinv, det, tau,
+                                                                status, counts);
     else
       k_inv_det_vec4<ALG, STAT><<<blocks, kThreads, 0, s>>>(z, n, ld, zinv, det, tau, status,
                                                             counts);

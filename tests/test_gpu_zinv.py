@@ -170,6 +170,59 @@ def test_fp64_flag_and_counts(zlib, orc):
     assert ei.max() < 4 * 2.0 ** -24 and ed.max() < 4 * 2.0 ** -24
 
 
+@pytest.mark.parametrize("density", [0.0, 0.01, 0.5, 1.0])
+@pytest.mark.parametrize("flags", [2, 3])
+def test_fp64_queue_is_position_independent(zlib, orc, density, flags):
+    """The FP64 variants queue flagged pixels per warp and recompute them 32 at
+    a time.  A pixel's outputs must not depend on where it sits, on how many of
+    its neighbours are flagged, on the layout (128-bit path, unaligned plane
+    stride on the one-pixel path, in place) or on the run: every arrangement
+    gives the same bits, and the flagged pixels match the oracle to FP32
+    rounding."""
+    rng = np.random.default_rng(11 + int(100 * density) + flags)
+    n = 40001  # a ragged tail after the last float4 group
+    well = S.WORKLOADS["scale_16k"].packed_z(np.arange(n, dtype=np.uint64))
+    ill = S.WORKLOADS["precision_4k"].packed_z(np.arange(n, dtype=np.uint64))
+    # precision_4k pixels with det/(adf) far below tau are flagged; scale_16k's are not
+    pick = rng.random(n) < density
+    z_np = np.where(pick[None, :], ill, well).astype(np.float32)
+    tau = 2.0 ** -10
+    z = torch.from_numpy(z_np).cuda()
+    zinv, det, st, cnt = zlib.zinv_det(z, flags, tau, want_status=True, want_counts=True)
+    perm = rng.permutation(n)
+    zp_, dp_, sp_ = zlib.zinv_det(z[:, perm].contiguous(), flags, tau, want_status=True)
+    inv_perm = np.argsort(perm)
+    zu = strided(z_np, odd_ld(n))  # one-pixel path, FP64 inline
+    zu_inv, zu_det, zu_st = zlib.zinv_det(zu, flags, tau, want_status=True)
+    zi = z.clone()
+    d_ip = torch.empty(n, device="cuda")
+    zlib.zinv_det(zi, flags, tau, out=(zi, d_ip))
+    again = zlib.zinv_det(z, flags, tau, want_status=True)
+    torch.cuda.synchronize()
+    a_inv, a_det, a_st = zinv.cpu().numpy(), det.cpu().numpy(), st.cpu().numpy()
+    for other_inv, other_det in ((zp_.cpu().numpy()[:, inv_perm], dp_.cpu().numpy()[inv_perm]),
+                                 (zu_inv.cpu().numpy(), zu_det.cpu().numpy()),
+                                 (zi.cpu().numpy(), d_ip.cpu().numpy()),
+                                 (again[0].cpu().numpy(), again[1].cpu().numpy())):
+        assert np.array_equal(a_inv.view(np.uint32), other_inv.view(np.uint32))
+        assert np.array_equal(a_det.view(np.uint32), other_det.view(np.uint32))
+    assert np.array_equal(a_st, sp_.cpu().numpy()[inv_perm])
+    assert np.array_equal(a_st, zu_st.cpu().numpy())
+    rec = (a_st & 2) > 0
+    assert int(cnt[1]) == int(rec.sum()) and int(cnt[0]) == int(((a_st & 1) > 0).sum())
+    if density == 0.0:
+        assert not rec.any()
+    if density == 1.0:
+        assert rec.mean() > 0.4
+    ref_inv, ref_det = orc.zinv_det(z_np)
+    assert np.array_equal((a_st & 1) > 0, ~(ref_det > 0))
+    good = rec & (ref_det > 0)
+    if good.any():
+        ei = inv_err(a_inv[:, good], ref_inv[:, good])
+        ed = det_err(a_det[good], ref_det[good])
+        assert ei.max() < 4 * 2.0 ** -24 and ed.max() < 4 * 2.0 ** -24
+
+
 U32 = 2.0 ** -24
 
 
