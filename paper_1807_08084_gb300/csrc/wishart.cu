@@ -24,10 +24,16 @@
 //   the outer loop and the nine channels unrolled (Z in registers); date 1's Z
 //   stays in registers while date 2's is summed, then both are written over
 //   the products half a tile at a time for the log-dets: ~52 KB per CTA, four
-//   CTAs per SM.
+//   CTAs per SM.  The log-dets take two outputs per pass with the compensated
+//   arithmetic on packed float2 pairs (f32x2: one instruction for both, each
+//   half rounded as the scalar operation, so the same bits).
 //   Backward: blocks are loaded directly; the window is summed one channel at a
 //   time (the registers go to the 49 tap accumulators); Z, then the packed
-//   M_t, are parked in shared memory for the correlations.
+//   M_t, are parked in shared memory for the correlations; the inverses run
+//   as packed pairs where registers allow (3 x 3 and 5 x 5 windows).
+//   (Packed FFMA2 in the window sums themselves ran 11% slower: adjacent
+//   outputs need odd-offset input pairs, which cost register moves, and
+//   GB300's FMA pipe does no more FMAs per cycle packed than scalar.)
 // Each tile writes its partial sums (FP64) to the workspace; a one-block-per-
 // output kernel adds them in tile order.  No float atomics: the results are the
 // same bits on every run.
@@ -365,23 +371,30 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
           }
         }
         __syncthreads();
+        // two outputs per pass (o and o + kWT, added to qsum in that order):
+        // the three compensated dets of both run as packed pairs
 #pragma unroll 1
-        for (int o = threadIdx.x; o < HALF; o += kWT) {
-          const int64_t gy = ty0 + 8 * h + o / kTW, gx = tx0 + o % kTW;
-          if (gy >= a.H || gx >= a.W) continue;
-          float z1[9], z2[9], z12[9];
+        for (int o = threadIdx.x; o < HALF; o += 2 * kWT) {
+          float2 z1[9], z2[9], z12[9];
 #pragma unroll
           for (int c = 0; c < 9; ++c) {
-            z1[c] = P[c * HALF + o];
-            z2[c] = P[(9 + c) * HALF + o];
-            z12[c] = z1[c] + z2[c];
+            z1[c] = make_float2(P[c * HALF + o], P[c * HALF + o + kWT]);
+            z2[c] = make_float2(P[(9 + c) * HALF + o], P[(9 + c) * HALF + o + kWT]);
+            z12[c] = add_rn(z1[c], z2[c]);
           }
-          const float l1 = log_dd(det_comp<float>(z1));
-          const float l2 = log_dd(det_comp<float>(z2));
-          const float l12 = log_dd(det_comp<float>(z12));
-          const float q = (l1 + l2) - 2.0f * l12 + six_ln2;
-          if (a.q_map) a.q_map[gy * a.W + gx] = q;
-          qsum += (double)q;
+          const float2 l1 = log_dd(det_comp<float2>(z1));
+          const float2 l2 = log_dd(det_comp<float2>(z2));
+          const float2 l12 = log_dd(det_comp<float2>(z12));
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int oe = o + e * kWT;
+            const int64_t gy = ty0 + 8 * h + oe / kTW, gx = tx0 + oe % kTW;
+            if (gy >= a.H || gx >= a.W) continue;
+            const float q = e == 0 ? (l1.x + l2.x) - 2.0f * l12.x + six_ln2
+                                   : (l1.y + l2.y) - 2.0f * l12.y + six_ln2;
+            if (a.q_map) a.q_map[gy * a.W + gx] = q;
+            qsum += (double)q;
+          }
         }
       }
     }
@@ -389,6 +402,69 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
     if (threadIdx.x == 0) a.partial[tile] = s;
   }
   cp_async_wait<0>();
+}
+
+// M_t of one output o in packed gradient form over the Z slots of G, from
+// the inverses W_1, W_2, W_12: M_t = W_t - 2 W_12, off-diagonal packed reals
+// doubled; zero outside the image.
+__device__ __forceinline__ void store_m(const WsArgs& a, float* G, int64_t ty0, int64_t tx0,
+                                        int o, const float w1[9], const float w2[9],
+                                        const float w12[9]) {
+  const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
+  const bool inside = gy < a.H && gx < a.W;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const float two = (c == 0 || c == 5 || c == 8) ? 1.0f : 2.0f;
+    G[c * kTH * kTW + o] = inside ? two * fmaf(-2.0f, w12[c], w1[c]) : 0.0f;
+    G[(9 + c) * kTH * kTW + o] = inside ? two * fmaf(-2.0f, w12[c], w2[c]) : 0.0f;
+  }
+}
+
+// The three compensated inverses of every output of the tile, over the Z
+// slots of G (output o = tid + kWT j, so a warp reads one row's 32 entries of
+// a plane).  PAIRED: two outputs per pass (o and o + kWT) as packed pairs,
+// for the 3 x 3 and 5 x 5 windows; the 7 x 7 kernel, at its register limit
+// with the 49 tap accumulators live, ran 3% slower that way and takes one.
+template <bool PAIRED>
+__device__ __forceinline__ void bwd_inverses(const WsArgs& a, float* G, int64_t ty0,
+                                             int64_t tx0) {
+  if constexpr (PAIRED) {
+#pragma unroll 1
+    for (int o = threadIdx.x; o < kTH * kTW; o += 2 * kWT) {
+      float2 z1[9], z2[9], z12[9], w1[9], w2[9], w12[9], d;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        z1[c] = make_float2(G[c * kTH * kTW + o], G[c * kTH * kTW + o + kWT]);
+        z2[c] = make_float2(G[(9 + c) * kTH * kTW + o], G[(9 + c) * kTH * kTW + o + kWT]);
+        z12[c] = add_rn(z1[c], z2[c]);
+      }
+      adjugate_inv_det_comp<float2>(z1, w1, d);
+      adjugate_inv_det_comp<float2>(z2, w2, d);
+      adjugate_inv_det_comp<float2>(z12, w12, d);
+      float v1[9], v2[9], v12[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) v1[c] = w1[c].x, v2[c] = w2[c].x, v12[c] = w12[c].x;
+      store_m(a, G, ty0, tx0, o, v1, v2, v12);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) v1[c] = w1[c].y, v2[c] = w2[c].y, v12[c] = w12[c].y;
+      store_m(a, G, ty0, tx0, o + kWT, v1, v2, v12);
+    }
+  } else {
+#pragma unroll 1
+    for (int o = threadIdx.x; o < kTH * kTW; o += kWT) {
+      float z1[9], z2[9], z12[9], w1[9], w2[9], w12[9], d;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        z1[c] = G[c * kTH * kTW + o];
+        z2[c] = G[(9 + c) * kTH * kTW + o];
+        z12[c] = z1[c] + z2[c];
+      }
+      adjugate_inv_det_comp<float>(z1, w1, d);
+      adjugate_inv_det_comp<float>(z2, w2, d);
+      adjugate_inv_det_comp<float>(z12, w12, d);
+      store_m(a, G, ty0, tx0, o, w1, w2, w12);
+    }
+  }
 }
 
 template <int R>
@@ -431,31 +507,9 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
       }
       if (phase == 1) {
         // per output: three compensated inverses, M_t = W_t - 2 W_12 in packed
-        // gradient form over the Z slots.  Output o = tid + kWT j, so a warp
-        // reads one row's 32 entries of a plane.
+        // gradient form over the Z slots
         __syncthreads();
-#pragma unroll 1
-        for (int o = threadIdx.x; o < kTH * kTW; o += kWT) {
-          const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
-          float z1[9], z2[9], z12[9], w1[9], w2[9], w12[9], d;
-#pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            z1[c] = G[c * kTH * kTW + o];
-            z2[c] = G[(9 + c) * kTH * kTW + o];
-            z12[c] = z1[c] + z2[c];
-          }
-          const bool inside = gy < a.H && gx < a.W;
-          adjugate_inv_det_comp<float>(z1, w1, d);
-          adjugate_inv_det_comp<float>(z2, w2, d);
-          adjugate_inv_det_comp<float>(z12, w12, d);
-#pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            // packed M_t = W_t - 2 W_12; off-diagonal packed reals count twice
-            const float two = (c == 0 || c == 5 || c == 8) ? 1.0f : 2.0f;
-            G[c * kTH * kTW + o] = inside ? two * fmaf(-2.0f, w12[c], w1[c]) : 0.0f;
-            G[(9 + c) * kTH * kTW + o] = inside ? two * fmaf(-2.0f, w12[c], w2[c]) : 0.0f;
-          }
-        }
+        bwd_inverses<(R < 3)>(a, G, ty0, tx0);
         __syncthreads();
       }
       if (phase > 0) {
