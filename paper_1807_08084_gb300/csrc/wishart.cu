@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
   extern __shared__ __align__(16) float smem[];
   float* P = smem;
   float* G = smem + T::P_FLOATS;  // [2][9][kTH][kTW]: Z_t, then the packed M_t
-  double* red = reinterpret_cast<double*>(G + 2 * T::Z_FLOATS);  // [kWT / 32][K]
+  static_assert(T::K * (kWT + 1) <= T::P_FLOATS, "the tap partials fit in P");
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
   const int y0 = 2 * (threadIdx.x / kTX), x0 = 4 * (threadIdx.x % kTX);
@@ -545,20 +545,26 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
         }
       }
     }
-    // fixed-order reduction of the K taps over the block
-    const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double vsum = (double)acc[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) vsum += __shfl_down_sync(0xffffffffu, vsum, o);
-      if (lane_id == 0) red[warp * K + k] = vsum;
-    }
+    // Fixed-order sum of the K taps over the block: the threads' accumulators
+    // go to shared memory (P is free: [K][kWT + 1], conflict-free both ways),
+    // then thread k adds tap k over the block's threads in thread order with
+    // TwoSum (compensated FP32, as accurate as FP64 for 64 terms) and stores it
+    // as a double.  An FP64 shuffle tree per tap kept GB300's FP64 pipe, at
+    // 1/64 of the FP32 rate, 28% busy.
     __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      double ssum = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) ssum += red[w * K + k];
-      a.partial[tile * K + k] = ssum;
+    float* accs = P;
+#pragma unroll
+    for (int k = 0; k < K; ++k) accs[k * (kWT + 1) + threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += kWT) {
+      float sum = 0.0f, err = 0.0f;
+#pragma unroll 8
+      for (int t = 0; t < kWT; ++t) {
+        float e;
+        two_sum(sum, accs[k * (kWT + 1) + t], sum, e);
+        err += e;
+      }
+      a.partial[tile * K + k] = (double)sum + (double)err;
     }
   }
 }
@@ -592,7 +598,7 @@ size_t fwd_smem() {
 template <int R>
 size_t bwd_smem() {
   using T = WTile<R>;
-  return (T::P_FLOATS + 2 * T::Z_FLOATS) * sizeof(float) + (kWT / 32) * T::K * sizeof(double);
+  return (T::P_FLOATS + 2 * T::Z_FLOATS) * sizeof(float);
 }
 
 int64_t tile_count(int64_t H, int64_t W) {
