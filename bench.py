@@ -236,6 +236,16 @@ def cpu_oracle_baseline(z_dev: torch.Tensor, budget_s: float = 12.0):
                       f"inverse and det, single thread ({spent:.1f} s)"}
 
 
+def workload_config(H: int, W: int, world: int) -> dict:
+    """The `config` of both arms' JSON lines: the scale_16k workload."""
+    n = H * W
+    return {"workload": f"scale_16k: {H}x{W} packed FP32 Hermitian Z ({n:,} matrices), "
+                        "N=16 looks, 8 class covariances in 512x512 blocks",
+            "matrices_per_gpu": n, "bytes_per_step_per_gpu": BYTES_FWD * n,
+            "l2": f"inputs larger than L2 ({BYTES_FWD * n / 1e9:.1f} GB streamed per step)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, world, rank):
     """The FP64 oracle timed on the host cores (the reference arm)."""
     if rank != 0:
@@ -257,10 +267,12 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{w.name}: first {m} of 16384x16384 packed Z, N=16 looks, "
-                                   "8 classes in 512x512 blocks (bounded CPU sample)"},
+            "config": workload_config(w.H, w.W, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "host": host_cpu(), "sample": f"{m} matrices per step"},
+                             "host": host_cpu(),
+                             "sample": f"the first {m} matrices of the {w.H}x{w.W} image per "
+                                       "step, FP64 Gauss-Jordan inverse and det, single "
+                                       "thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -492,13 +504,7 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"scale_16k: {w.H}x{w.W} packed FP32 Hermitian Z "
-                                   f"({n:,} matrices), N=16 looks, 8 class covariances "
-                                   "in 512x512 blocks",
-                       "matrices_per_gpu": n, "bytes_per_step_per_gpu": BYTES_FWD * n,
-                       "l2": f"inputs larger than L2 ({BYTES_FWD * n / 1e9:.1f} GB streamed "
-                             "per step)",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(w.H, w.W, world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak,
                          "traffic": traffic, "peak_kind": peak_kind,
