@@ -89,7 +89,13 @@ const char* zinv_status_string(int code);
  *   flags  ZINV_PLAIN, or ZINV_COMPENSATED and/or ZINV_FP64_RECOMPUTE.
  *   tau    threshold of ZINV_FP64_RECOMPUTE: a pixel is recomputed in FP64 when
  *          !(det > tau*a*d*f) (Hadamard: 0 < det <= a*d*f for positive definite
- *          Z).  Must be finite and >= 0; ignored without the flag.
+ *          Z), or when |det| is outside [2^-100, 2^100).  Must be finite and
+ *          >= 0; ignored without the flag.
+ *          Range: det scales with the cube of the entries.  Without the flag
+ *          the FP32 routes need det and 1/det to be normal floats (entries
+ *          roughly within 1e-12 .. 1e12); with it, pixels beyond that band are
+ *          recomputed in FP64 and get the correctly rounded Z^-1 (det itself
+ *          rounds to 0 or inf where it is outside the FP32 range).
  *   status [n] optional (NULL): per-pixel ZINV_PIX_* bits.
  *   counts [2] optional (NULL), device int64: overwritten with the number of
  *          pixels flagged ZINV_PIX_NOT_PD and ZINV_PIX_RECOMPUTED.

@@ -262,10 +262,17 @@ __device__ __forceinline__ void cholesky_inv_det(const float x[9], float w[9], f
 // Flagged-pixel recompute (not in the paper; it follows its stability
 // discussion in §3.3).  Hadamard's inequality gives det/(a d f) in (0, 1] for
 // positive definite Z; a small ratio means cancellation ate the FP32 digits.
-// !(>) also catches NaN and det <= 0.
+// !(>) also catches NaN and det <= 0.  A det whose magnitude is outside
+// [2^-100, 2^100) is flagged too: det scales with the cube of the entries, so
+// for entries beyond about 1e+-10 the terms of the expansion or det itself
+// leave the FP32 normal range (underflow loses their digits; overflow or 1/det
+// out of range ruins Z^-1, although Z^-1 is representable); FP64's range
+// covers such pixels.  Inside the band every term is normal down to 2^-26 of
+// det, so the FP32 results are exact multiples of the unscaled ones.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool needs_recompute(float det, const float x[9], float tau) {
-  return !(det > tau * (x[0] * x[5] * x[8]));
+  const unsigned e = (__float_as_uint(det) >> 23) & 0xffu;  // biased exponent of |det|
+  return !(det > tau * (x[0] * x[5] * x[8])) || e - 27u >= 200u;
 }
 
 // The compensated route in FP64 on the FP32 inputs: their products and the

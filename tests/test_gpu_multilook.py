@@ -63,6 +63,37 @@ def test_boxcar_small_images(zlib, orc, win, mode, shape):
     assert torch.equal(zinv, zinv2) and torch.equal(det, det2)
 
 
+@pytest.mark.parametrize("mode", list(MODES))
+def test_power_of_two_scaling(zlib, orc, mode):
+    """Single-look data scaled by 2^j gives window covariances scaled by 2^2j:
+    Z^-1 comes out scaled by 2^-2j bit for bit while det stays a normal float
+    (j = +-8).  At j = +-30 det leaves the FP32 range; the FP64-recompute
+    modes take every pixel to FP64 and match the oracle there."""
+    w = S.scaled(S.WORKLOADS["multilook_8k"], 37, 131)
+    s_np = w.image()
+    base_inv, base_det = (t.cpu().numpy() for t in zlib.multilook_zinv_det(
+        torch.from_numpy(s_np).cuda(), 5, None, MODES[mode]))
+    for j in (-8, 8):
+        sj = (s_np * np.float32(2.0 ** j)).astype(np.complex64)
+        inv, det = (t.cpu().numpy() for t in zlib.multilook_zinv_det(
+            torch.from_numpy(sj).cuda(), 5, None, MODES[mode]))
+        assert np.array_equal(inv.view(np.uint32),
+                              np.ldexp(base_inv, -2 * j).astype(np.float32).view(np.uint32))
+        assert np.array_equal(det.view(np.uint32),
+                              np.ldexp(base_det, 6 * j).astype(np.float32).view(np.uint32))
+    if not MODES[mode] & 2:
+        return
+    for j in (-30, 30):
+        sj = (s_np * np.float32(2.0 ** j)).astype(np.complex64)
+        inv, det, st = (t.cpu().numpy() for t in zlib.multilook_zinv_det(
+            torch.from_numpy(sj).cuda(), 5, None, MODES[mode], want_status=True))
+        assert np.all(st == 2)
+        assert np.all(det == 0) if j < 0 else np.all(np.isinf(det))
+        ref_inv, _, cond, _ = reference(orc, sj, 5)
+        # Z itself is accumulated in FP32 on chip: the usual 1e-5 cond
+        assert np.all(inv_err(inv.reshape(9, -1), ref_inv) <= 1e-5 * cond)
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (3, 2), (5, 200)])
 def test_degenerate_shapes(zlib, orc, shape):
     """Images smaller than the window: clamp-to-edge everywhere."""

@@ -223,6 +223,60 @@ def test_fp64_queue_is_position_independent(zlib, orc, density, flags):
         assert ei.max() < 4 * 2.0 ** -24 and ed.max() < 4 * 2.0 ** -24
 
 
+@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+def test_power_of_two_scaling(zlib, orc, flags):
+    """Algorithm 2 is homogeneous and power-of-two scaling is exact, so Z 2^j
+    gives Z^-1 2^-j and det 2^3j bit for bit while det stays a normal float
+    (j = +-20).  det scales with the cube of the entries: at 2^+-36 and 2^+-60
+    det leaves the band [2^-100, 2^100) and the FP64-recompute modes take those
+    pixels to FP64, whose range covers them: Z^-1 within FP32 rounding of the
+    oracle, det the FP32 rounding of the exact det (0 or inf where that is out
+    of range), the pixels positive definite."""
+    w = S.WORKLOADS["plain_256"]
+    n = 4099
+    z_np = w.packed_z(np.arange(n, dtype=np.uint64))
+    base_inv, base_det, base_st = (t.cpu().numpy() for t in zlib.zinv_det(
+        torch.from_numpy(z_np).cuda(), flags, want_status=True))
+    for j in (-20, 20):
+        zj = np.ldexp(z_np, j).astype(np.float32)
+        assert np.array_equal(np.ldexp(zj, -j), z_np)  # the scaled input is exact
+        inv, det, st = (t.cpu().numpy() for t in zlib.zinv_det(
+            torch.from_numpy(zj).cuda(), flags, want_status=True))
+        assert np.array_equal(inv.view(np.uint32),
+                              np.ldexp(base_inv, -j).astype(np.float32).view(np.uint32))
+        assert np.array_equal(det.view(np.uint32),
+                              np.ldexp(base_det, 3 * j).astype(np.float32).view(np.uint32))
+        assert np.array_equal(st, base_st)
+    if not flags & 2:
+        return
+    assert np.all((base_st == 0) | (base_st == 2))
+    for j in (-60, -36, 36, 60):
+        zj = np.ldexp(z_np, j).astype(np.float32)
+        inv, det, st = (t.cpu().numpy() for t in zlib.zinv_det(
+            torch.from_numpy(zj).cuda(), flags, want_status=True))
+        # det of Z 2^j is base_det 2^3j: out of [2^-100, 2^100) -> FP64
+        scaled = np.ldexp(base_det.astype(np.float64), 3 * j)
+        out = ~((scaled >= 2.0 ** -100) & (scaled < 2.0 ** 100))
+        assert np.all((st == 0) | (st == 2)) and np.all(st[out] == 2)
+        assert np.all(st[base_st == 2] == 2)
+        if abs(j) == 60:
+            assert out.all()
+        keep = st == 0  # the FP32 route in range: exactly the scaled bits
+        assert np.array_equal(inv[:, keep].view(np.uint32),
+                              np.ldexp(base_inv[:, keep], -j).astype(np.float32).view(np.uint32))
+        assert np.array_equal(det[keep].view(np.uint32), scaled[keep].astype(np.float32).view(np.uint32))
+        out = st == 2  # recomputed in FP64: FP32 rounding of the exact result
+        ref_inv, ref_det = orc.zinv_det(zj)
+        assert np.all(inv_err(inv[:, out], ref_inv[:, out]) < 4 * 2.0 ** -24)
+        with np.errstate(over="ignore"):  # dets beyond FP32 become inf
+            e32 = ref_det.astype(np.float32)
+        normal = out & np.isfinite(e32) & (e32 >= np.float32(2.0 ** -126))
+        assert np.all(det_err(det[normal], ref_det[normal]) < 4 * 2.0 ** -24)
+        assert np.all(np.isinf(det[out & np.isinf(e32)]))
+        sub = out & np.isfinite(e32) & (e32 < np.float32(2.0 ** -126))
+        assert np.all(np.abs(det[sub].astype(np.float64) - e32[sub]) <= 2.0 ** -149)
+
+
 U32 = 2.0 ** -24
 
 
