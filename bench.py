@@ -236,6 +236,11 @@ def cpu_oracle_baseline(z_dev: torch.Tensor, budget_s: float = 12.0):
                       f"inverse and det, single thread ({spent:.1f} s)"}
 
 
+def fp32_peak_tflops() -> float:
+    """FP32 FMA peak of a GB300: 152 SMs x 128 lanes x 2 flops x 2.07 GHz."""
+    return 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def workload_config(H: int, W: int, world: int) -> dict:
     """The `config` of both arms' JSON lines: the scale_16k workload."""
     n = H * W
@@ -391,6 +396,17 @@ def main():
             gbs = 64 * wl.n / (t * 1e-3) / 1e9
             multilook[f"win{win}"] = {"gpix_s": wl.n / (t * 1e-3) / 1e9, "ms": t, "gbs": gbs,
                                       "frac_hbm": gbs / hbm_peak}
+        # learnable 7 x 7 window (general weights: 441 window FMAs per pixel)
+        g = np.exp(-0.5 * (np.arange(-3, 4) / 1.5) ** 2)
+        wts = torch.from_numpy((np.outer(g, g) / np.outer(g, g).sum()).astype(np.float32)).cuda()
+        t = timed(lambda: zp.multilook_zinv_det(sl, 7, wts, zp.PLAIN, out=(ml_inv, ml_det)),
+                  sub, args.warmup, world)
+        gbs = 64 * wl.n / (t * 1e-3) / 1e9
+        tflops = 2 * 9 * 49 * wl.n / (t * 1e-3) / 1e12
+        multilook["weighted7"] = {"gpix_s": wl.n / (t * 1e-3) / 1e9, "ms": t, "gbs": gbs,
+                                  "frac_hbm": gbs / hbm_peak, "window_tflops": tflops,
+                                  "frac_alu": tflops / fp32_peak_tflops(),
+                                  "weights": "7 x 7 Gaussian, sigma 1.5, normalised"}
         del sl, ml_inv, ml_det
 
     # --- multifrequency: three bands, block-diagonal pixels (8192 x 8192) -------
@@ -460,7 +476,7 @@ def main():
         # algorithmic FP32 work: the window sums, 2 dates x 49 taps x 9 channels FMA
         # per pixel forward; the backward recomputes them and correlates as many
         fl_f, fl_b = 2 * 2 * 49 * 9, 2 * 2 * 2 * 49 * 9
-        alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        alu_peak = fp32_peak_tflops()
         for name, t, fl in (("forward", t_f, fl_f), ("backward", t_b, fl_b)):
             tf = fl * ww.n / (t * 1e-3) / 1e12
             wishart[name] = {"gpix_s": ww.n / (t * 1e-3) / 1e9, "ms": t, "tflops": tf,

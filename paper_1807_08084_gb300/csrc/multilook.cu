@@ -20,11 +20,17 @@
 //   - phase V: vertical window sums over the ring (four rows per thread), scale
 //     by 1/N, invert, store (warp-contiguous along x).
 // Each input row is loaded once per strip (plus 2r rows at a segment start and
-// 2r halo columns): ~1.1x the ideal read traffic.  The weighted window uses a
-// simpler tiled kernel.
+// 2r halo columns): ~1.1x the ideal read traffic.
+//
+// Weighted windows (general taps, not separable) of 3 x 3, 5 x 5 and 7 x 7 run
+// on the window engine of window.cuh (32 x 16 output tiles, 4 x 2 outputs per
+// thread, cp.async staging of the next tile behind the window sums); Z then
+// waits in shared memory and a warp inverts one row of 32 outputs at a time.
+// Other odd windows up to 15 x 15 use a simpler tiled kernel.
 #include "async.cuh"
 #include "common.cuh"
 #include "pixel.cuh"
+#include "window.cuh"
 
 namespace zinv {
 
@@ -398,6 +404,73 @@ __global__ void __launch_bounds__(kMlThreads) k_multilook_weighted(MlArgs a) {
   if (STAT && a.counts) add_counts(a.counts, c0, c1);
 }
 
+// Weighted window of 2R + 1 (R = 1..3) on the window engine of window.cuh.
+// Per tile: the staged single-look block's products, the window sums of all
+// nine channels in registers (each output's taps in row-major order, as the
+// simpler kernel adds them), Z parked in shared memory over the products, then
+// per output Algorithm 2 and the stores (a warp covers 32 outputs of a row).
+template <int R, int ALG, bool STAT>
+__global__ void __launch_bounds__(win::kWT, 4) k_multilook_window(MlArgs a) {
+  using T = win::WTile<R>;
+  constexpr int TILE = win::kTH * win::kTW;
+  extern __shared__ __align__(16) float smem[];
+  float* P = smem;  // products [9][SH][SWP], then the tile's Z [9][TILE]
+  float2* Sb = reinterpret_cast<float2*>(smem + T::P_FLOATS);  // next single-look block
+  float* wsh = reinterpret_cast<float*>(Sb + T::S_F2);         // taps [L][WROW]
+  const int64_t tiles_x = (a.W + win::kTW - 1) / win::kTW;
+  const int64_t tiles = tiles_x * ((a.H + win::kTH - 1) / win::kTH);
+  const int y0 = 2 * (threadIdx.x / win::kTX), x0 = 4 * (threadIdx.x % win::kTX);
+  uint32_t c0 = 0, c1 = 0;
+  win::stage_taps<R>(a.weights, wsh);
+  if ((int64_t)blockIdx.x < tiles)
+    win::issue_block<R>(a.s, a.plane_ld, a.H, a.W, blockIdx.x, Sb);
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t ty0 = (tile / tiles_x) * win::kTH, tx0 = (tile % tiles_x) * win::kTW;
+    cp_async_wait<0>();
+    __syncthreads();  // the block is in Sb; P is free (the last tile's Z is read)
+    win::block_products<R>(Sb, P);
+    __syncthreads();  // Sb is free; P holds the products
+    const int64_t next = tile + gridDim.x;
+    if (next < tiles) win::issue_block<R>(a.s, a.plane_ld, a.H, a.W, next, Sb);
+    float z[9][2][4];
+    win::window_all<R>(P, wsh, y0, x0, z);
+    __syncthreads();  // the products are read; P takes the tile's Z
+#pragma unroll
+    for (int c = 0; c < 9; ++c) win::store_block(P + c * TILE, y0, x0, z[c]);
+    __syncthreads();
+#pragma unroll 1
+    for (int o = threadIdx.x; o < TILE; o += win::kWT) {
+      const int64_t gy = ty0 + o / win::kTW, gx = tx0 + o % win::kTW;
+      if (gy >= a.H || gx >= a.W) continue;
+      float zz[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) zz[c] = P[c * TILE + o];
+      finish_pixel<ALG, STAT>(a, gy, gx, zz, c0, c1);
+    }
+  }
+  cp_async_wait<0>();
+  if (STAT && a.counts) add_counts(a.counts, c0, c1);
+}
+
+template <int R>
+constexpr size_t window_smem() {
+  using T = win::WTile<R>;
+  return (T::P_FLOATS + T::L * T::WROW) * sizeof(float) + T::S_F2 * sizeof(float2);
+}
+
+template <typename K>
+int launch_window(K kernel, size_t smem, const MlArgs& a, cudaStream_t s) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return ZINV_ERR_LAUNCH;
+  }
+  const int64_t tiles = ((a.W + win::kTW - 1) / win::kTW) * ((a.H + win::kTH - 1) / win::kTH);
+  const int64_t blocks = cover_blocks(tiles * win::kWT, win::kWT);
+  kernel<<<(unsigned)blocks, win::kWT, smem, s>>>(a);
+  return launch_status();
+}
+
 template <typename K>
 int launch_ml(K kernel, size_t smem, const MlArgs& a, cudaStream_t s) {
   static_assert(sizeof(K) > 0, "");
@@ -427,8 +500,14 @@ int launch_strip(K kernel, size_t smem, const MlArgs& a, cudaStream_t s) {
 
 template <int ALG, bool STAT>
 int dispatch_ml(const MlArgs& a, cudaStream_t s) {
-  if (a.weights)
+  if (a.weights) {
+    switch (a.win) {
+      case 3: return launch_window(k_multilook_window<1, ALG, STAT>, window_smem<1>(), a, s);
+      case 5: return launch_window(k_multilook_window<2, ALG, STAT>, window_smem<2>(), a, s);
+      case 7: return launch_window(k_multilook_window<3, ALG, STAT>, window_smem<3>(), a, s);
+    }
     return launch_ml(k_multilook_weighted<ALG, STAT>, kWSmem, a, s);
+  }
   switch (a.win) {
     case 3: return launch_strip(k_multilook_strip<1, ALG, STAT>, Strip<1>::smem, a, s);
     case 5: return launch_strip(k_multilook_strip<2, ALG, STAT>, Strip<2>::smem, a, s);

@@ -112,19 +112,26 @@ def test_degenerate_shapes(zlib, orc, shape):
             check(zinv, det, ref, "plain_fp64", sel=ok)
 
 
-@pytest.mark.parametrize("win", [1, 3, 7, 9])
-def test_weighted_window(zlib, orc, win):
-    H, W = 45, 70
+@pytest.mark.parametrize("win", [1, 3, 5, 7, 9])
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("shape", [(45, 70), (32, 64), (5, 3), (17, 33)])
+def test_weighted_window(zlib, orc, win, mode, shape):
+    """General (non-separable) taps: 3 x 3 to 7 x 7 on the tiled window kernel,
+    other sizes on the simpler one; ragged tiles, exact tile multiples (32 x 16
+    tiles), images smaller than the window, every mode, against the oracle."""
+    H, W = shape
     w = S.scaled(S.WORKLOADS["wishart_pair_4k"], H, W)
     s_np = w.image(0)
     rng = np.random.default_rng(win)
     wts = rng.uniform(0.2, 1.0, win * win).astype(np.float32)
     s = torch.from_numpy(s_np).cuda()
-    zinv, det = zlib.multilook_zinv_det(s, win, torch.from_numpy(wts).cuda(), 2)
+    zinv, det = zlib.multilook_zinv_det(s, win, torch.from_numpy(wts).cuda(), MODES[mode])
+    zinv2, det2 = zlib.multilook_zinv_det(s, win, torch.from_numpy(wts).cuda(), MODES[mode])
     torch.cuda.synchronize()
+    assert torch.equal(zinv, zinv2) and torch.equal(det, det2)
     if win == 1:  # single look: rank one, det 0
         return
-    check(zinv, det, reference(orc, s_np, win, wts), "plain_fp64")
+    check(zinv, det, reference(orc, s_np, win, wts), mode)
 
 
 def test_weighted_equals_boxcar(zlib, orc):
@@ -149,9 +156,10 @@ def test_argument_errors(zlib):
 
 
 def test_full_size_crops(zlib, orc):
-    """8192 x 8192 generated on the GPU, all three windows in the launch
-    configuration of the full image; 12 crops (corners, edges, interior) against
-    the oracle on inputs regenerated by the numpy twin."""
+    """8192 x 8192 generated on the GPU, the three boxcar windows and two
+    weighted ones (the benchmark's 7 x 7 Gaussian taps, random 5 x 5 taps) in
+    the launch configuration of the full image; 12 crops (corners, edges,
+    interior) against the oracle on inputs regenerated by the numpy twin."""
     from paper_1807_08084_gb300.synth import gpu as G
     w = S.WORKLOADS["multilook_8k"]
     s = G.image(w)
@@ -159,9 +167,13 @@ def test_full_size_crops(zlib, orc):
     rng = np.random.default_rng(9)
     boxes = [(0, 0), (0, W - 48), (H - 48, 0), (H - 48, W - 48), (0, 4000), (4000, 0),
              (H - 48, 5000), (6000, W - 48)] + [tuple(rng.integers(100, 8000, 2)) for _ in range(4)]
-    for win in (3, 5, 7):
+    g = np.exp(-0.5 * (np.arange(-3, 4) / 1.5) ** 2)
+    gauss7 = (np.outer(g, g) / np.outer(g, g).sum()).astype(np.float32)  # the bench's taps
+    rand5 = np.random.default_rng(5).uniform(0.2, 1.0, 25).astype(np.float32)
+    for win, wts in ((3, None), (5, None), (7, None), (7, gauss7), (5, rand5)):
         r = (win - 1) // 2
-        zinv, det = zlib.multilook_zinv_det(s, win, None, 2)
+        wt = None if wts is None else torch.from_numpy(wts.ravel()).cuda()
+        zinv, det = zlib.multilook_zinv_det(s, win, wt, 2)
         torch.cuda.synchronize()
         for (y0, x0) in boxes:
             y1, x1 = y0 + 48, x0 + 48
@@ -172,7 +184,7 @@ def test_full_size_crops(zlib, orc):
             crop = w.looks(idx).reshape(3, cy1 - cy0, cx1 - cx0)
             got_in = s[:, cy0:cy1, cx0:cx1].cpu().numpy()
             np.testing.assert_array_equal(got_in, crop)
-            ref = reference(orc, crop, win)
+            ref = reference(orc, crop, win, None if wts is None else wts.ravel())
             ch, cw = cy1 - cy0, cx1 - cx0
             inner = np.zeros((ch, cw), bool)
             inner[y0 - cy0:y1 - cy0, x0 - cx0:x1 - cx0] = True
