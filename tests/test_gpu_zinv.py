@@ -430,3 +430,24 @@ def test_host_streaming_matches_device(zlib):
     # pageable input cannot be read by the kernel: it needs the staged way
     with pytest.raises(RuntimeError):
         zlib.zinv_det_host(z.clone())
+
+
+def test_host_streaming_fp64_recompute(zlib):
+    """The FP64-recompute variant queues flagged pixels and parks their inputs
+    in the outputs: through the staged path (in place in device chunks) and the
+    direct path (the kernel on pinned host memory) it gives the device result
+    bit for bit on an image where half the pixels are flagged."""
+    w = S.WORKLOADS["precision_4k"]
+    n = 300_007
+    z = torch.from_numpy(w.packed_z(np.arange(n, dtype=np.uint64)))
+    z_pin = z.pin_memory()
+    flags = zlib.COMPENSATED | zlib.FP64_RECOMPUTE
+    ref_inv, ref_det, st, cnt = zlib.zinv_det(z.cuda(), flags, want_status=True,
+                                              want_counts=True)
+    assert int(cnt[1]) > n // 3
+    ws = torch.empty(zlib.zinv_det_host_workspace_bytes(65536), dtype=torch.uint8,
+                     device="cuda")
+    for args in ((ws, flags | zlib.HOST_STAGED), (None, flags)):
+        zinv_h, det_h = zlib.zinv_det_host(z_pin, *args)
+        torch.cuda.synchronize()
+        assert torch.equal(zinv_h, ref_inv.cpu()) and torch.equal(det_h, ref_det.cpu())
