@@ -24,7 +24,6 @@ namespace {
 constexpr int kNT = 256;
 constexpr int kNW = 32;  // tile width
 constexpr int kNH = 8;   // tile height
-constexpr int kMaxRadius = 15;
 
 struct NlmArgs {
   const float* z;
@@ -94,33 +93,91 @@ __global__ void __launch_bounds__(kNT) k_nlm(NlmArgs a) {
     const int dy1 = (int)(gy + RAD >= a.H ? a.H - 1 - gy : RAD);
     const int dx0 = (int)(gx - RAD < 0 ? -gx : -RAD);
     const int dx1 = (int)(gx + RAD >= a.W ? a.W - 1 - gx : RAD);
-    float acc[9];
+    float out[9], wsum;
+    if constexpr (METHOD == 0) {
+      // Algorithm 2: neighbours two at a time (dx, dx + 1); the sums, the pair
+      // determinants and the weighted accumulation run on packed float2 pairs
+      // (f32x2, each half rounded as the scalar operation), the logs and exp2s
+      // stay scalar; even and odd neighbours accumulate in the two halves.
+      float2 zi2[9], acc[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = 0.0f;
-    float wsum = 0.0f;
-    for (int dy = dy0; dy <= dy1; ++dy) {
-      const int row = cy + dy;
-      for (int dx = dx0; dx <= dx1; ++dx) {
-        const int col = cx + dx;
-        float zj[9], zs[9];
+      for (int c = 0; c < 9; ++c) {
+        zi2[c] = make_float2(zi[c], zi[c]);
+        acc[c] = make_float2(0.0f, 0.0f);
+      }
+      float2 ws = make_float2(0.0f, 0.0f);
+      for (int dy = dy0; dy <= dy1; ++dy) {
+        const int row = cy + dy;
+        const float* lrow = Ls + row * SW + cx;
+        int dx = dx0;
+        for (; dx < dx1; dx += 2) {
+          const int col = cx + dx;
+          float2 zj[9], zs[9];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-          zj[c] = Zs[(c * SH + row) * SW + col];
-          zs[c] = zi[c] + zj[c];
+          for (int c = 0; c < 9; ++c) {
+            const float* q = Zs + (c * SH + row) * SW + col;
+            zj[c] = make_float2(q[0], q[1]);
+            zs[c] = add_rn(zi2[c], zj[c]);
+          }
+          const float2 det = det_adjugate<float2>(zs);
+          // ln det((Zi+Zj)/2) = ln det(Zi+Zj) - 3 ln 2
+          const float d0 = (logf(det.x) - three_ln2) - 0.5f * (li + lrow[dx]);
+          const float d1 = (logf(det.y) - three_ln2) - 0.5f * (li + lrow[dx + 1]);
+          const float2 w =
+              make_float2(exp2f(a.c * fmaxf(d0, 0.0f)), exp2f(a.c * fmaxf(d1, 0.0f)));
+#pragma unroll
+          for (int c = 0; c < 9; ++c) acc[c] = fma_rn(w, zj[c], acc[c]);
+          ws = add_rn(ws, w);
         }
-        const float det = METHOD == 0 ? det_adjugate(zs) : det_cholesky(zs);
-        // ln det((Zi+Zj)/2) = ln det(Zi+Zj) - 3 ln 2
-        const float dist = (logf(det) - three_ln2) - 0.5f * (li + Ls[row * SW + col]);
-        const float w = exp2f(a.c * fmaxf(dist, 0.0f));
+        if (dx == dx1) {  // an odd count leaves one neighbour: the first halves
+          const int col = cx + dx;
+          float zj[9], zs[9];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) acc[c] = fmaf(w, zj[c], acc[c]);
-        wsum += w;
+          for (int c = 0; c < 9; ++c) {
+            zj[c] = Zs[(c * SH + row) * SW + col];
+            zs[c] = add_rn(zi[c], zj[c]);
+          }
+          const float det = det_adjugate<float>(zs);
+          const float d0 = (logf(det) - three_ln2) - 0.5f * (li + lrow[dx]);
+          const float w = exp2f(a.c * fmaxf(d0, 0.0f));
+#pragma unroll
+          for (int c = 0; c < 9; ++c) acc[c].x = fmaf(w, zj[c], acc[c].x);
+          ws.x += w;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 9; ++c) out[c] = acc[c].x + acc[c].y;
+      wsum = ws.x + ws.y;
+    } else {
+      // Algorithm 1: one neighbour at a time (pairing its scalar square roots
+      // and reciprocals only cost it registers)
+#pragma unroll
+      for (int c = 0; c < 9; ++c) out[c] = 0.0f;
+      wsum = 0.0f;
+      for (int dy = dy0; dy <= dy1; ++dy) {
+        const int row = cy + dy;
+        for (int dx = dx0; dx <= dx1; ++dx) {
+          const int col = cx + dx;
+          float zj[9], zs[9];
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            zj[c] = Zs[(c * SH + row) * SW + col];
+            zs[c] = zi[c] + zj[c];
+          }
+          const float det = det_cholesky(zs);
+          // ln det((Zi+Zj)/2) = ln det(Zi+Zj) - 3 ln 2
+          const float dist = (logf(det) - three_ln2) - 0.5f * (li + Ls[row * SW + col]);
+          const float w = exp2f(a.c * fmaxf(dist, 0.0f));
+#pragma unroll
+          for (int c = 0; c < 9; ++c) out[c] = fmaf(w, zj[c], out[c]);
+          wsum += w;
+        }
       }
     }
     const float inv = 1.0f / wsum;
     const int64_t p = gy * a.W + gx;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) a.out[c * n + p] = acc[c] * inv;
+    for (int c = 0; c < 9; ++c) a.out[c * n + p] = out[c] * inv;
   }
 }
 

@@ -190,16 +190,19 @@ __device__ __forceinline__ dd<T> det_comp(const T x[9]) {
 }
 
 // det alone by Alg. 2's first-column cofactor expansion (the a_c, b_c, c_c of
-// Eq. adjoint_elements in Eq. detr), plain FP32.
-__device__ __forceinline__ float det_adjugate(const float x[9]) {
-  const float a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
-  const float d = x[5], er = x[6], ei = x[7], f = x[8];
-  const float ac = d * f - (er * er + ei * ei);
-  const float bcr = (cr * er + ci * ei) - br * f;
-  const float bci = (ci * er - cr * ei) - bi * f;
-  const float ccr = (br * er - bi * ei) - cr * d;
-  const float cci = (br * ei + bi * er) - ci * d;
-  return a * ac + br * bcr + bi * bci + cr * ccr + ci * cci;
+// Eq. adjoint_elements in Eq. detr), plain FP32.  T = float, or float2 for two
+// matrices at once; every operation is an explicit product or FMA, so both
+// forms round alike.
+template <typename T>
+__device__ __forceinline__ T det_adjugate(const T x[9]) {
+  const T a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
+  const T d = x[5], er = x[6], ei = x[7], f = x[8];
+  const T ac = fma_rn(-er, er, fma_rn(-ei, ei, mul_rn(d, f)));   // d f - |e|^2
+  const T bcr = fma_rn(-br, f, fma_rn(cr, er, mul_rn(ci, ei)));  // Re(c conj(e)) - Re(b) f
+  const T bci = fma_rn(-bi, f, fma_rn(ci, er, mul_rn(-cr, ei)));
+  const T ccr = fma_rn(-cr, d, fma_rn(br, er, mul_rn(-bi, ei)));
+  const T cci = fma_rn(-ci, d, fma_rn(br, ei, mul_rn(bi, er)));
+  return fma_rn(ci, cci, fma_rn(cr, ccr, fma_rn(bi, bci, fma_rn(br, bcr, mul_rn(a, ac)))));
 }
 
 // ln det, from hi + lo: ln(hi) + ln(1 + lo/hi) with |lo/hi| <= 2^-24.
