@@ -54,3 +54,27 @@ def test_blockdiag_flags_bad_block(zlib):
     torch.cuda.synchronize()
     s = st.cpu().numpy()
     assert (s[7] & 1) and int(cnt[0]) == 1 and int((s & 1).sum()) == 1
+
+
+def test_blockdiag_full_size_sampled(zlib, orc):
+    """Three bands of 8192 x 8192 pixels built as the benchmark builds them, in
+    its launch configuration; 60k sampled pixels against the oracle's inverse of
+    the full 9 x 9 matrix, on inputs regenerated by the numpy twin."""
+    from dataclasses import replace
+    from paper_1807_08084_gb300.synth import gpu as G
+    wb = S.scaled(S.WORKLOADS["scale_16k"], 8192, 8192)
+    ws = [replace(wb, seed=wb.seed + 17 * b) for b in range(3)]
+    zb = torch.stack([G.packed_z(w) for w in ws])
+    zinv, det = zlib.zinv_det_blockdiag(zb)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(17)
+    idx = np.unique(np.concatenate([rng.integers(0, wb.n, 60000), [0, wb.n - 1]]))
+    it = torch.from_numpy(idx).cuda()
+    z_np = np.stack([w.packed_z(idx.astype(np.uint64)) for w in ws])
+    np.testing.assert_array_equal(zb.reshape(3, 9, -1)[:, :, it].cpu().numpy(), z_np)
+    ref_inv, ref_det, _ = orc.zinv_det_blockdiag(z_np, 3)
+    cond = np.max(np.stack([orc.cond(z_np[b]) for b in range(3)]), axis=0)
+    zi = zinv.reshape(3, 9, -1)[:, :, it].cpu().numpy()
+    for b in range(3):
+        assert np.all(inv_err(zi[b], ref_inv[b]) <= 1e-5 * cond)
+    assert np.all(det_err(det.reshape(-1)[it].cpu().numpy(), ref_det) <= 3e-5 * cond)

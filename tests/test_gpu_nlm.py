@@ -69,3 +69,28 @@ def test_bad_arguments(zlib):
         args.update(kw)
         with pytest.raises(RuntimeError):
             zlib.nlm_wishart(z, args["radius"], args["looks"], args["h"], args["method"])
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_full_size_sampled(zlib, orc, method):
+    """The benchmark's 1024 x 1024 image, radius 11 (23 x 23 window), in its
+    launch configuration.  A pixel's output depends only on its search window,
+    so corner, edge and interior pixels are checked against the oracle run on a
+    crop holding that window (clipped by the image as the full image clips it)."""
+    from paper_1807_08084_gb300.synth import gpu as G
+    R, N = 11, 1024
+    w = S.scaled(S.WORKLOADS["scale_16k"], N, N)
+    z = G.packed_z(w)
+    out = zlib.nlm_wishart(z, R, 16.0, 1.0, method).reshape(9, N, N)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(23)
+    pts = [(0, 0), (0, N - 1), (N - 1, 0), (N - 1, N - 1), (5, 500), (700, N - 3)]
+    pts += [tuple(int(v) for v in rng.integers(R, N - R, 2)) for _ in range(6)]
+    for (y, x) in pts:
+        y0, y1, x0, x1 = max(0, y - R), min(N, y + R + 1), max(0, x - R), min(N, x + R + 1)
+        yy, xx = np.meshgrid(np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+        crop = w.packed_z((yy * N + xx).ravel().astype(np.uint64))
+        ch, cw = y1 - y0, x1 - x0
+        ref = orc.nlm_wishart(crop, ch, cw, R, 16.0, 1.0)[:, (y - y0) * cw + (x - x0)]
+        got = out[:, y, x].cpu().numpy()
+        assert rel_err(got[:, None], ref[:, None]).max() <= TOL, (y, x)

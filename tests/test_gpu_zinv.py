@@ -358,6 +358,26 @@ def test_scale_workload_full_size_sampled(zlib, orc):
     assert det_err(det.reshape(-1)[-1:].cpu().numpy(), ref_det)[0] < 1e-3
 
 
+def test_paper_sim_full_size_sampled(zlib, orc):
+    """The paper's simulated set (its Table 2: 5,469,354 matrices A = R R^H)
+    generated on the GPU as one row, in the benchmark's launch configuration
+    (a plane stride that is not a multiple of four: the one-pixel kernel);
+    100k sampled pixels and the last one against the oracle, both routes."""
+    from paper_1807_08084_gb300.synth import gpu as G
+    w = S.WORKLOADS["paper_sim"]
+    z = G.packed_z(w)
+    rng = np.random.default_rng(8)
+    idx = np.unique(np.concatenate([rng.integers(0, w.n, 100000), [w.n - 1]]))
+    it = torch.from_numpy(idx).cuda()
+    z_np = w.packed_z(idx.astype(np.uint64))
+    np.testing.assert_array_equal(z.reshape(9, -1)[:, it].cpu().numpy(), z_np)
+    for mode in ("plain", "cholesky"):
+        zinv, det = run_mode(zlib, z, mode)
+        torch.cuda.synchronize()
+        check_parity(orc, z_np, zinv.reshape(9, -1)[:, it].cpu().numpy(),
+                     det.reshape(-1)[it].cpu().numpy())
+
+
 def _bwd_tol_check(orc, z_np, gz_gpu, gW, gd, gl, tol=TOL):
     ref = orc.zinv_det_bwd(z_np, gW, gd, gl)
     W, det = orc.zinv_det(z_np)
