@@ -40,7 +40,6 @@ struct WTile {
   static constexpr int WROW = 8;                           // tap rows padded for 128-bit loads
   static constexpr int S_F2 = 3 * SH * SW;                 // one date's single-look block (float2)
   static_assert(P_FLOATS % 4 == 0 && S_F2 % 2 == 0, "16-byte aligned regions");
-  static_assert(P_FLOATS >= 2 * 9 * (kTH / 2) * kTW, "half a tile's Z of both dates fits in P");
 };
 
 __device__ __forceinline__ int64_t clampi(int64_t v, int64_t hi) {

@@ -22,11 +22,11 @@
 //   Forward: each date's single-look block is copied with cp.async while the
 //   other date's window sums run; the window is summed with the input rows as
 //   the outer loop and the nine channels unrolled (Z in registers); date 1's Z
-//   stays in registers while date 2's is summed, then both are written over
-//   the products half a tile at a time for the log-dets: ~52 KB per CTA, four
-//   CTAs per SM.  The log-dets take two outputs per pass with the compensated
-//   arithmetic on packed float2 pairs (f32x2: one instruction for both, each
-//   half rounded as the scalar operation, so the same bits).
+//   stays in registers while date 2's is summed, and each thread then takes
+//   the log-dets of its own eight outputs from registers, two adjacent
+//   outputs per pass with the compensated arithmetic on packed float2 pairs
+//   (f32x2: one instruction for both, each half rounded as the scalar
+//   operation).  ~52 KB of shared memory per CTA, four CTAs per SM.
 //   Backward: blocks are loaded directly; the window is summed one channel at a
 //   time (the registers go to the 49 tap accumulators); Z, then the packed
 //   M_t, are parked in shared memory for the correlations; the inverses run
@@ -169,15 +169,13 @@ template <int R>
 __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
   using T = WTile<R>;
   extern __shared__ __align__(16) float smem[];
-  float* P = smem;  // one date's products [9][SH][SWP]; then Z of half a tile [2][9][kTH/2][kTW]
+  float* P = smem;  // one date's products [9][SH][SWP]
   float2* Sb = reinterpret_cast<float2*>(smem + T::P_FLOATS);  // next single-look block
   float* wsh = reinterpret_cast<float*>(Sb + T::S_F2);         // taps [L][WROW]
   double* red = reinterpret_cast<double*>(wsh + T::L * T::WROW);
-  constexpr int HALF = kTH / 2 * kTW;  // outputs in half a tile (one warp's rows)
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
   const int y0 = 2 * (threadIdx.x / kTX), x0 = 4 * (threadIdx.x % kTX);
-  const int warp = threadIdx.x >> 5;  // warp w owns tile rows 8w .. 8w + 7
   const float six_ln2 = 4.15888308335967185650f;
   stage_taps<R>(a.weights, wsh);
   if ((int64_t)blockIdx.x < tiles) issue_block<R>(a.s[0], a.plane_ld, a.H, a.W, blockIdx.x, Sb);
@@ -206,30 +204,20 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
             for (int i = 0; i < 4; ++i) z0[c][r][i] = z[c][r][i];
         continue;
       }
-      // Both dates' Z are in registers.  Per half tile (one warp's rows): that
-      // warp writes them over the products, then all threads take the
-      // compensated log-dets of Z1, Z2 and Z1 + Z2 of its 256 outputs
-      // (output o: row o / kTW, so a warp reads one row's 32 entries of a plane).
-#pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        __syncthreads();  // P is free: products read (h = 0), half 0 done (h = 1)
-        if (warp == h) {
+      // Both dates' Z are in registers: the thread takes the compensated
+      // log-dets of Z1, Z2 and Z1 + Z2 of its own 4 x 2 outputs, two adjacent
+      // outputs per pass on packed float2 pairs, and stores and adds its q in
+      // row-major order.
 #pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            store_block(P + c * HALF, y0 - 8 * h, x0, z0[c]);
-            store_block(P + (9 + c) * HALF, y0 - 8 * h, x0, z[c]);
-          }
-        }
-        __syncthreads();
-        // two outputs per pass (o and o + kWT, added to qsum in that order):
-        // the three compensated dets of both run as packed pairs
-#pragma unroll 1
-        for (int o = threadIdx.x; o < HALF; o += 2 * kWT) {
+      for (int r = 0; r < 2; ++r) {
+        const int64_t gy = ty0 + y0 + r;
+#pragma unroll
+        for (int i = 0; i < 4; i += 2) {
           float2 z1[9], z2[9], z12[9];
 #pragma unroll
           for (int c = 0; c < 9; ++c) {
-            z1[c] = make_float2(P[c * HALF + o], P[c * HALF + o + kWT]);
-            z2[c] = make_float2(P[(9 + c) * HALF + o], P[(9 + c) * HALF + o + kWT]);
+            z1[c] = make_float2(z0[c][r][i], z0[c][r][i + 1]);
+            z2[c] = make_float2(z[c][r][i], z[c][r][i + 1]);
             z12[c] = add_rn(z1[c], z2[c]);
           }
           const float2 l1 = log_dd(det_comp<float2>(z1));
@@ -237,8 +225,7 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
           const float2 l12 = log_dd(det_comp<float2>(z12));
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            const int oe = o + e * kWT;
-            const int64_t gy = ty0 + 8 * h + oe / kTW, gx = tx0 + oe % kTW;
+            const int64_t gx = tx0 + x0 + i + e;
             if (gy >= a.H || gx >= a.W) continue;
             const float q = e == 0 ? (l1.x + l2.x) - 2.0f * l12.x + six_ln2
                                    : (l1.y + l2.y) - 2.0f * l12.y + six_ln2;
