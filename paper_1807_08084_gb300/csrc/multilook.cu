@@ -24,7 +24,8 @@
 //
 // Weighted windows (general taps, not separable) of 3 x 3, 5 x 5 and 7 x 7 run
 // on the window engine of window.cuh (32 x 16 output tiles, 4 x 2 outputs per
-// thread, cp.async staging of the next tile behind the window sums); Z then
+// thread, two channels per packed FMA, cp.async staging of the next tile
+// behind the window sums); Z then
 // waits in shared memory and a warp inverts one row of 32 outputs at a time.
 // Other odd windows up to 15 x 15 use a simpler tiled kernel.
 #include "async.cuh"
@@ -417,26 +418,26 @@ __global__ void __launch_bounds__(win::kWT, 4) k_multilook_window(MlArgs a) {
   using T = win::WTile<R>;
   constexpr int TILE = win::kTH * win::kTW;
   extern __shared__ __align__(16) float smem[];
-  float* P = smem;  // products [9][SH][SWP], then the tile's Z [9][TILE]
+  float* P = smem;  // channel-paired products, then the tile's Z [9][TILE]
   float2* Sb = reinterpret_cast<float2*>(smem + T::P_FLOATS);  // next single-look block
-  float* wsh = reinterpret_cast<float*>(Sb + T::S_F2);         // taps [L][WROW]
+  float2* wsh2 = reinterpret_cast<float2*>(Sb + T::S_F2);      // duplicated taps [L][WROW]
   const int64_t tiles_x = (a.W + win::kTW - 1) / win::kTW;
   const int64_t tiles = tiles_x * ((a.H + win::kTH - 1) / win::kTH);
   const int y0 = 2 * (threadIdx.x / win::kTX), x0 = 4 * (threadIdx.x % win::kTX);
   uint32_t c0 = 0, c1 = 0;
-  win::stage_taps<R>(a.weights, wsh);
+  win::stage_taps_paired<R>(a.weights, wsh2);
   if ((int64_t)blockIdx.x < tiles)
     win::issue_block<R>(a.s, a.plane_ld, a.H, a.W, blockIdx.x, Sb);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * win::kTH, tx0 = (tile % tiles_x) * win::kTW;
     cp_async_wait<0>();
     __syncthreads();  // the block is in Sb; P is free (the last tile's Z is read)
-    win::block_products<R>(Sb, P);
+    win::block_products_paired<R>(Sb, P);
     __syncthreads();  // Sb is free; P holds the products
     const int64_t next = tile + gridDim.x;
     if (next < tiles) win::issue_block<R>(a.s, a.plane_ld, a.H, a.W, next, Sb);
     float z[9][2][4];
-    win::window_all<R>(P, wsh, y0, x0, z);
+    win::window_all_paired<R>(P, wsh2, y0, x0, z);
     __syncthreads();  // the products are read; P takes the tile's Z
 #pragma unroll
     for (int c = 0; c < 9; ++c) win::store_block(P + c * TILE, y0, x0, z[c]);
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(win::kWT, 4) k_multilook_window(MlArgs a) {
 template <int R>
 constexpr size_t window_smem() {
   using T = win::WTile<R>;
-  return (T::P_FLOATS + T::L * T::WROW) * sizeof(float) + T::S_F2 * sizeof(float2);
+  return T::P_FLOATS * sizeof(float) + (T::L * T::WROW + T::S_F2) * sizeof(float2);
 }
 
 template <typename K>

@@ -5,9 +5,11 @@
 // 4 x 2 block of them, so every input row it loads from shared memory feeds
 // two output rows.  The tile's single-look block (tile plus an R-pixel halo,
 // clamp-to-edge) is copied with cp.async into Sb; its nine channel products
-// (the packed entries of s s^H) go to P [9][SH][SWP]; window_all sums a
-// (2R+1)^2 window of them for all nine channels, the input rows as the outer
-// loop, with each output's taps added in row-major order.
+// (the packed entries of s s^H) go to P in the channel-paired layout below;
+// window_all_paired sums a (2R+1)^2 window of them for all nine channels, the
+// input rows as the outer loop, with each output's taps added in row-major
+// order, two channels per packed f32x2 FMA.  (The Wishart backward keeps the
+// scalar layout P [9][SH][SWP] and sums one channel at a time.)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -71,68 +73,6 @@ __device__ __forceinline__ void load_row(const float* src, float (&row)[4 * WTil
   }
 }
 
-// One input row of all nine channels for the thread's 4 x 2 outputs: the row
-// y0 + iy feeds output row 0 with tap row iy (ROW0) and output row 1 with tap
-// row iy - 1 (ROW1).  Taps come from the shared table wsh [L][WROW].
-template <int R, bool ROW0, bool ROW1>
-__device__ __forceinline__ void row_step(const float* P, const float* wsh, int iy, int y0,
-                                         int x0, float (&z)[9][2][4]) {
-  using T = WTile<R>;
-  constexpr int L = T::L;
-  float w0[2 * 4], w1[2 * 4];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    if (ROW0) {
-      const float4 q = *reinterpret_cast<const float4*>(wsh + iy * T::WROW + 4 * h);
-      w0[4 * h] = q.x, w0[4 * h + 1] = q.y, w0[4 * h + 2] = q.z, w0[4 * h + 3] = q.w;
-    }
-    if (ROW1) {
-      const float4 q = *reinterpret_cast<const float4*>(wsh + (iy - 1) * T::WROW + 4 * h);
-      w1[4 * h] = q.x, w1[4 * h + 1] = q.y, w1[4 * h + 2] = q.z, w1[4 * h + 3] = q.w;
-    }
-  }
-  const float* src = P + (y0 + iy) * T::SWP + x0;
-#pragma unroll
-  for (int c = 0; c < 9; ++c) {
-    float row[4 * T::NV];
-    load_row<R>(src + c * T::PLANE, row);
-#pragma unroll
-    for (int dx = 0; dx < L; ++dx)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (ROW0) z[c][0][i] = fmaf(w0[dx], row[i + dx], z[c][0][i]);
-        if (ROW1) z[c][1][i] = fmaf(w1[dx], row[i + dx], z[c][1][i]);
-      }
-  }
-}
-
-// Window sums of all nine channels for the thread's 4 x 2 outputs from one
-// date's staged products P: the L + 1 input rows in order, the first and last
-// feeding one output row each.  Per output the taps are added in row-major
-// order, as in window_4x2.
-template <int R>
-__device__ __forceinline__ void window_all(const float* P, const float* wsh, int y0, int x0,
-                                           float (&z)[9][2][4]) {
-  constexpr int L = WTile<R>::L;
-#pragma unroll
-  for (int c = 0; c < 9; ++c)
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) z[c][r][i] = 0.0f;
-  row_step<R, true, false>(P, wsh, 0, y0, x0, z);
-#pragma unroll 1
-  for (int iy = 1; iy < L; ++iy) row_step<R, true, true>(P, wsh, iy, y0, x0, z);
-  row_step<R, false, true>(P, wsh, L, y0, x0, z);
-}
-
-// Copies the taps into the shared table [L][WROW] (pad entries unused).
-template <int R>
-__device__ __forceinline__ void stage_taps(const float* weights, float* wsh) {
-  using T = WTile<R>;
-  for (int k = threadIdx.x; k < T::K; k += kWT) wsh[(k / T::L) * T::WROW + k % T::L] = weights[k];
-}
-
 // Issues, as one cp.async group, the copies of an image's single-look block of
 // a tile plus halo (clamp-to-edge) into Sb [3][SH][SW]; s holds the three
 // component planes of an H x W image, plane_ld apart.
@@ -151,17 +91,131 @@ __device__ __forceinline__ void issue_block(const float2* s, int64_t plane_ld, i
   cp_async_commit();
 }
 
-// The nine channel products of the staged block Sb -> P[c][SH][SWP].
+// Channel-paired products.  The window sums of window_all_paired run on
+// packed f32x2 FMAs with a pair of channels per instruction: channels (0, 1),
+// (2, 3), (4, 5) and (6, 7) are stored as float2 planes [SH][SWP] over the
+// memory of the scalar planes 2j and 2j + 1, channel 8 as scalar plane 8.
+// Within a row the 16-byte unit u (float2 columns 2u and 2u + 1) sits at unit
+// u ^ ((u >> 3) & 1): the eight threads of a quarter-warp read units 2t + q
+// (t = 0..7) of one row, which that spreads over the eight 16-byte bank groups
+// for every q (with units in plain order, t and t + 4 would collide).
+__device__ __forceinline__ int pcol(int x) { return x ^ ((x >> 3) & 2); }
+
+// The nine channel products of the staged block Sb in the channel-paired layout.
 template <int R>
-__device__ __forceinline__ void block_products(const float2* Sb, float* P) {
+__device__ __forceinline__ void block_products_paired(const float2* Sb, float* P) {
   using T = WTile<R>;
+  float2* P2 = reinterpret_cast<float2*>(P);
   for (int i = threadIdx.x; i < T::SH * T::SW; i += kWT) {
     const int r = i / T::SW, x = i - r * T::SW;
     float p[9];
     products(Sb[i], Sb[T::SH * T::SW + i], Sb[2 * T::SH * T::SW + i], p);
+    const int o = r * T::SWP + pcol(x);
 #pragma unroll
-    for (int c = 0; c < 9; ++c) P[c * T::PLANE + r * T::SWP + x] = p[c];
+    for (int j = 0; j < 4; ++j) P2[j * T::PLANE + o] = make_float2(p[2 * j], p[2 * j + 1]);
+    P[8 * T::PLANE + r * T::SWP + x] = p[8];
   }
+}
+
+// Copies the taps, each duplicated into both halves of a float2, into the
+// shared table [L][WROW] of float2 (the packed FMAs' weight operand).
+template <int R>
+__device__ __forceinline__ void stage_taps_paired(const float* weights, float2* wsh2) {
+  using T = WTile<R>;
+  for (int k = threadIdx.x; k < T::K; k += kWT) {
+    const float w = weights[k];
+    wsh2[(k / T::L) * T::WROW + k % T::L] = make_float2(w, w);
+  }
+}
+
+// One input row of all nine channels for the thread's 4 x 2 outputs: the row
+// y0 + iy feeds output row 0 with tap row iy (ROW0) and output row 1 with tap
+// row iy - 1 (ROW1).  Channel pairs take one packed FMA per tap and output
+// (each half rounded as a scalar fmaf, so the sums are the bits of the scalar
+// loop), channel 8 a scalar one.  On GB300 a packed FMA completes no more
+// FMAs per cycle than scalar ones, but it halves the instructions issued: the
+// weighted 7 x 7 multilook ran 2.38 -> 2.00 ms with it.
+template <int R, bool ROW0, bool ROW1>
+__device__ __forceinline__ void row_step_paired(const float* P, const float2* wsh2, int iy,
+                                                int y0, int x0, float2 (&zp)[4][2][4],
+                                                float (&z8)[2][4]) {
+  using T = WTile<R>;
+  constexpr int L = T::L;
+  constexpr int NU = 2 + R;  // 16-byte units of a row segment: 4 + 2R columns
+  float2 w0[L + 1], w1[L + 1];
+#pragma unroll
+  for (int h = 0; h < (L + 1) / 2; ++h) {
+    if (ROW0) {
+      const float4 q = *reinterpret_cast<const float4*>(wsh2 + iy * T::WROW + 2 * h);
+      w0[2 * h] = make_float2(q.x, q.y), w0[2 * h + 1] = make_float2(q.z, q.w);
+    }
+    if (ROW1) {
+      const float4 q = *reinterpret_cast<const float4*>(wsh2 + (iy - 1) * T::WROW + 2 * h);
+      w1[2 * h] = make_float2(q.x, q.y), w1[2 * h + 1] = make_float2(q.z, q.w);
+    }
+  }
+  const float2* src = reinterpret_cast<const float2*>(P) + (y0 + iy) * T::SWP;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2 row[2 * NU];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(src + j * T::PLANE + pcol(x0 + 2 * q));
+      row[2 * q] = make_float2(v.x, v.y);
+      row[2 * q + 1] = make_float2(v.z, v.w);
+    }
+#pragma unroll
+    for (int dx = 0; dx < L; ++dx)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (ROW0) zp[j][0][i] = __ffma2_rn(w0[dx], row[i + dx], zp[j][0][i]);
+        if (ROW1) zp[j][1][i] = __ffma2_rn(w1[dx], row[i + dx], zp[j][1][i]);
+      }
+  }
+  float row[4 * T::NV];
+  load_row<R>(P + 8 * T::PLANE + (y0 + iy) * T::SWP + x0, row);
+#pragma unroll
+  for (int dx = 0; dx < L; ++dx)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (ROW0) z8[0][i] = fmaf(w0[dx].x, row[i + dx], z8[0][i]);
+      if (ROW1) z8[1][i] = fmaf(w1[dx].x, row[i + dx], z8[1][i]);
+    }
+}
+
+// Window sums of all nine channels for the thread's 4 x 2 outputs from one
+// date's staged products P (channel-paired layout): the L + 1 input rows in
+// order, the first and last feeding one output row each.  Per output the taps
+// are added in row-major order.
+template <int R>
+__device__ __forceinline__ void window_all_paired(const float* P, const float2* wsh2, int y0,
+                                                  int x0, float (&z)[9][2][4]) {
+  constexpr int L = WTile<R>::L;
+  float2 zp[4][2][4];
+  float z8[2][4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) zp[j][r][i] = make_float2(0.0f, 0.0f);
+      z8[r][i] = 0.0f;
+    }
+  row_step_paired<R, true, false>(P, wsh2, 0, y0, x0, zp, z8);
+#pragma unroll 1
+  for (int iy = 1; iy < L; ++iy) row_step_paired<R, true, true>(P, wsh2, iy, y0, x0, zp, z8);
+  row_step_paired<R, false, true>(P, wsh2, L, y0, x0, zp, z8);
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        z[2 * j][r][i] = zp[j][r][i].x;
+        z[2 * j + 1][r][i] = zp[j][r][i].y;
+      }
+      z[8][r][i] = z8[r][i];
+    }
 }
 
 // Stores the thread's 4 x 2 block of one channel into a [kTH][kTW] plane.

@@ -21,7 +21,8 @@
 // tile and its halo sit in shared memory at a time.
 //   Forward: each date's single-look block is copied with cp.async while the
 //   other date's window sums run; the window is summed with the input rows as
-//   the outer loop and the nine channels unrolled (Z in registers); date 1's Z
+//   the outer loop and the nine channels unrolled, two channels per packed
+//   f32x2 FMA (window_all_paired of window.cuh; Z in registers); date 1's Z
 //   stays in registers while date 2's is summed, and each thread then takes
 //   the log-dets of its own eight outputs from registers, two adjacent
 //   outputs per pass with the compensated arithmetic on packed float2 pairs
@@ -31,9 +32,9 @@
 //   time (the registers go to the 49 tap accumulators); Z, then the packed
 //   M_t, are parked in shared memory for the correlations; the inverses run
 //   as packed pairs where registers allow (3 x 3 and 5 x 5 windows).
-//   (Packed FFMA2 in the window sums themselves ran 11% slower: adjacent
-//   outputs need odd-offset input pairs, which cost register moves, and
-//   GB300's FMA pipe does no more FMAs per cycle packed than scalar.)
+//   (Packed FMAs over pairs of adjacent output columns instead of channel
+//   pairs ran 11% slower: they need odd-offset input pairs, which cost
+//   register moves.)
 // Each tile writes its partial sums (FP64) to the workspace; a one-block-per-
 // output kernel adds them in tile order.  No float atomics: the results are the
 // same bits on every run.
@@ -169,15 +170,15 @@ template <int R>
 __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
   using T = WTile<R>;
   extern __shared__ __align__(16) float smem[];
-  float* P = smem;  // one date's products [9][SH][SWP]
+  float* P = smem;  // one date's products, channel-paired layout
   float2* Sb = reinterpret_cast<float2*>(smem + T::P_FLOATS);  // next single-look block
-  float* wsh = reinterpret_cast<float*>(Sb + T::S_F2);         // taps [L][WROW]
-  double* red = reinterpret_cast<double*>(wsh + T::L * T::WROW);
+  float2* wsh2 = reinterpret_cast<float2*>(Sb + T::S_F2);      // duplicated taps [L][WROW]
+  double* red = reinterpret_cast<double*>(wsh2 + T::L * T::WROW);
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
   const int y0 = 2 * (threadIdx.x / kTX), x0 = 4 * (threadIdx.x % kTX);
   const float six_ln2 = 4.15888308335967185650f;
-  stage_taps<R>(a.weights, wsh);
+  stage_taps_paired<R>(a.weights, wsh2);
   if ((int64_t)blockIdx.x < tiles) issue_block<R>(a.s[0], a.plane_ld, a.H, a.W, blockIdx.x, Sb);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
@@ -187,14 +188,14 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
     for (int t = 0; t < 2; ++t) {
       cp_async_wait<0>();
       __syncthreads();  // date t's block is in Sb; P is free (and the taps are in place)
-      block_products<R>(Sb, P);
+      block_products_paired<R>(Sb, P);
       __syncthreads();  // Sb is free; P holds date t's products
       // the next block (date 2 of this tile, then date 1 of the next) loads
       // while this date's window sums run
       const int64_t next = t == 0 ? tile : tile + gridDim.x;
       if (next < tiles) issue_block<R>(a.s[1 - t], a.plane_ld, a.H, a.W, next, Sb);
       float z[9][2][4];
-      window_all<R>(P, wsh, y0, x0, z);
+      window_all_paired<R>(P, wsh2, y0, x0, z);
       if (t == 0) {
 #pragma unroll
         for (int c = 0; c < 9; ++c)
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(kRedThreads)
 template <int R>
 size_t fwd_smem() {
   using T = WTile<R>;
-  return (T::P_FLOATS + T::L * T::WROW) * sizeof(float) + T::S_F2 * sizeof(float2) +
+  return T::P_FLOATS * sizeof(float) + (T::L * T::WROW + T::S_F2) * sizeof(float2) +
          (kWT / 32) * sizeof(double);
 }
 template <int R>
