@@ -68,28 +68,24 @@ def load() -> ctypes.CDLL:
 
 
 def _declare_extra(lib):
-    """Entry points beyond the per-pixel ones, declared when present."""
-    if hasattr(lib, "multilook_zinv_det"):
-        lib.multilook_zinv_det.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
-                                           ctypes.c_uint32, ctypes.c_float, _P, _P, _P]
-        lib.multilook_zinv_det.restype = ctypes.c_int
-    if hasattr(lib, "zinv_det_blockdiag"):
-        lib.zinv_det_blockdiag.argtypes = [_P, ctypes.c_int, _I64, _I64, _P, _P, ctypes.c_uint32,
-                                           ctypes.c_float, _P, _P, _P]
-        lib.zinv_det_blockdiag.restype = ctypes.c_int
-    if hasattr(lib, "nlm_wishart"):
-        lib.nlm_wishart.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_float,
-                                    ctypes.c_float, ctypes.c_int, _P, _P]
-        lib.nlm_wishart.restype = ctypes.c_int
-    if hasattr(lib, "wishart_stat_fwd"):
-        lib.wishart_workspace_bytes.argtypes = [_I64, _I64, ctypes.c_int]
-        lib.wishart_workspace_bytes.restype = ctypes.c_size_t
-        lib.wishart_stat_fwd.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
-                                         _P, ctypes.c_size_t, _P]
-        lib.wishart_stat_fwd.restype = ctypes.c_int
-        lib.wishart_stat_bwd.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
-                                         _P, ctypes.c_size_t, _P]
-        lib.wishart_stat_bwd.restype = ctypes.c_int
+    """Signatures of the window, block-diagonal and nonlocal-means entry points."""
+    lib.multilook_zinv_det.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
+                                       ctypes.c_uint32, ctypes.c_float, _P, _P, _P]
+    lib.multilook_zinv_det.restype = ctypes.c_int
+    lib.zinv_det_blockdiag.argtypes = [_P, ctypes.c_int, _I64, _I64, _P, _P, ctypes.c_uint32,
+                                       ctypes.c_float, _P, _P, _P]
+    lib.zinv_det_blockdiag.restype = ctypes.c_int
+    lib.nlm_wishart.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_int, _P, _P]
+    lib.nlm_wishart.restype = ctypes.c_int
+    lib.wishart_workspace_bytes.argtypes = [_I64, _I64, ctypes.c_int]
+    lib.wishart_workspace_bytes.restype = ctypes.c_size_t
+    lib.wishart_stat_fwd.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
+                                     _P, ctypes.c_size_t, _P]
+    lib.wishart_stat_fwd.restype = ctypes.c_int
+    lib.wishart_stat_bwd.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
+                                     _P, ctypes.c_size_t, _P]
+    lib.wishart_stat_bwd.restype = ctypes.c_int
 
 
 def status_string(code: int) -> str:
