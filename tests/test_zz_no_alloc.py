@@ -65,3 +65,23 @@ def test_noalloc_rejects_images_beyond_its_scratch(zlib):
     H, W = 8200, 8192
     assert f(s.data_ptr(), s.data_ptr(), H, W, H * W, 7, wts.data_ptr(), None, loss.data_ptr(),
              stream) == -1
+
+
+def test_noalloc_at_its_maximum_size(zlib):
+    """8192 x 8192 pixels take all 131072 tiles of the fixed scratch: the largest
+    image the entry point accepts.  Same kernel and the same fixed-order reduction
+    as wishart_stat_fwd, so the loss and the q map are the same bits."""
+    from paper_1807_08084_gb300.synth import gpu as G
+    f = _entry(zlib)
+    w = S.scaled(S.WORKLOADS["wishart_pair_4k"], 8192, 8192)
+    s1, s2 = G.image(w, 0), G.image(w, 1)
+    wts = torch.full((49,), 1 / 49, device="cuda")
+    ref_loss, ref_q = zlib.wishart_stat_fwd(s1, s2, wts, 7, want_map=True)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    loss = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
+    q = torch.full((w.H, w.W), float("nan"), device="cuda")
+    assert f(s1.data_ptr(), s2.data_ptr(), w.H, w.W, w.H * w.W, 7, wts.data_ptr(), q.data_ptr(),
+             loss.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    assert float(loss) == float(ref_loss)
+    assert torch.equal(q, ref_q)
