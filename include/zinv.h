@@ -274,7 +274,10 @@ int wishart_stat_fwd_noalloc(const float* s1, const float* s2, int64_t H, int64_
  * The call is asynchronous with respect to the host and ordered after prior
  * work on `stream`; later work on `stream` waits for the last chunk to land.
  * The host buffers must stay valid until then.  Not re-entrant: two calls on
- * the same device must not overlap in time.
+ * the same device must not overlap in time.  If a staged call fails after it
+ * has queued copies, `stream` still waits for everything it queued (or the
+ * call waits on the host before returning), so synchronizing `stream` after
+ * an error is enough before the host buffers are freed or reused.
  */
 size_t zinv_det_host_workspace_bytes(int64_t chunk);
 int zinv_det_host(const float* z_host, int64_t n, int64_t ld, float* zinv_host,

@@ -68,7 +68,8 @@ def load() -> ctypes.CDLL:
 
 
 def _declare_extra(lib):
-    """Signatures of the window, block-diagonal and nonlocal-means entry points."""
+    """Signatures of the window, block-diagonal, nonlocal-means and Wishart entry points
+    (including the allocation-free Wishart forward)."""
     lib.multilook_zinv_det.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
                                        ctypes.c_uint32, ctypes.c_float, _P, _P, _P]
     lib.multilook_zinv_det.restype = ctypes.c_int
@@ -86,6 +87,9 @@ def _declare_extra(lib):
     lib.wishart_stat_bwd.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
                                      _P, ctypes.c_size_t, _P]
     lib.wishart_stat_bwd.restype = ctypes.c_int
+    lib.wishart_stat_fwd_noalloc.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
+                                             _P]
+    lib.wishart_stat_fwd_noalloc.restype = ctypes.c_int
 
 
 def status_string(code: int) -> str:

@@ -551,12 +551,27 @@ namespace {
 constexpr int64_t kNoAllocTiles = 131072;  // one slot per 32 x 16 tile: 8192 x 8192 pixels
 __device__ __align__(256) double g_noalloc_partials[kNoAllocTiles];
 
+// Device address of g_noalloc_partials per device.  A successful lookup is
+// kept; a failed one is not, so a later call on that device tries again.
 struct NoAllocScratch {
-  std::once_flag once;
-  cudaError_t err = cudaErrorNotReady;
+  std::mutex mu;
   double* ptr = nullptr;
 };
 NoAllocScratch g_noalloc[kMaxDevices];
+
+double* noalloc_scratch(int dev) {
+  NoAllocScratch& sc = g_noalloc[dev];
+  std::lock_guard<std::mutex> lock(sc.mu);
+  if (!sc.ptr) {
+    double* p = nullptr;
+    if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_partials) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    sc.ptr = p;
+  }
+  return sc.ptr;
+}
 }  // namespace
 }  // namespace zinv
 
@@ -579,12 +594,8 @@ extern "C" int wishart_stat_fwd_noalloc(const float* s1, const float* s2, int64_
   if (rc != ZINV_OK) return rc;
   // Host code cannot use g_noalloc_partials directly (here it names a host-side
   // stand-in); take the device address once per device, with that device current.
-  NoAllocScratch& sc = g_noalloc[dev];
-  std::call_once(sc.once, [&]() {
-    sc.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&sc.ptr), g_noalloc_partials);
-    if (sc.err != cudaSuccess) cudaGetLastError();
-  });
-  if (sc.err != cudaSuccess || !sc.ptr) return ZINV_ERR_LAUNCH;
+  double* scratch = noalloc_scratch(dev);
+  if (!scratch) return ZINV_ERR_LAUNCH;
   if (!device_accessible(s1) || !device_accessible(s2) || !device_accessible(weights) ||
       !device_accessible(d_loss) || (q_map && !device_accessible(q_map)))
     return ZINV_ERR_ARG;
@@ -596,7 +607,7 @@ extern "C" int wishart_stat_fwd_noalloc(const float* s1, const float* s2, int64_
   a.plane_ld = plane_ld;
   a.weights = weights;
   a.q_map = q_map;
-  a.partial = sc.ptr;  // every tile writes its own slot before the reduce reads it
+  a.partial = scratch;  // every tile writes its own slot before the reduce reads it
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (win) {
     case 3: rc = launch_tiles(k_wishart_fwd<1>, fwd_smem<1>(), a, st); break;

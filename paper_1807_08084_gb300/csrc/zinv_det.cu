@@ -23,6 +23,12 @@ namespace zinv {
 
 constexpr int kThreads = 256;
 
+// z and zinv carry no __restrict__: zinv == z (in place) is allowed, and the
+// FP64 queue reads back the inputs it parked in zinv.  Every access to them is
+// an explicit streaming load or store (__ldcs, __ldcg, __stcs), so the code
+// does not rely on the two being distinct.  det, status and counts never alias
+// an input.
+
 // Launch shape per variant, from sweeps on GB300 over the 16384 x 16384 image
 // (nothing flagged) and the 4096 x 4096 cond-controlled one (54% flagged).
 // The light variants stream best with one group of four pixels per thread.
@@ -41,8 +47,8 @@ constexpr int kGroupsPerThread =
 constexpr int kQueue = 160;
 
 template <int ALG, bool STAT>
-__device__ __forceinline__ void one_pixel(const float* __restrict__ z, int64_t ld, int64_t p,
-                                          float* __restrict__ zinv, float* __restrict__ det,
+__device__ __forceinline__ void one_pixel(const float* z, int64_t ld, int64_t p,
+                                          float* zinv, float* __restrict__ det,
                                           float tau, uint8_t* __restrict__ status, uint32_t& c0,
                                           uint32_t& c1) {
   float x[9], w[9], dt;
@@ -60,8 +66,8 @@ __device__ __forceinline__ void one_pixel(const float* __restrict__ z, int64_t l
 }
 
 template <int ALG, bool STAT>
-__device__ __forceinline__ void inv_det_vec4(const float* __restrict__ z, int64_t n, int64_t ld,
-                                             float* __restrict__ zinv, float* __restrict__ det,
+__device__ __forceinline__ void inv_det_vec4(const float* z, int64_t n, int64_t ld,
+                                             float* zinv, float* __restrict__ det,
                                              float tau, uint8_t* __restrict__ status,
                                              unsigned long long* __restrict__ counts) {
   const int64_t groups = n >> 2;
@@ -142,8 +148,8 @@ __device__ __forceinline__ int flush_rounds(const int64_t* q, int qn, int ln, in
 // FP64 results, the status byte (with NOT_PD from the FP64 det) and counts
 // NOT_PD.
 template <int ALG, bool STAT>
-__device__ __forceinline__ void inv_det_vec4_queued(const float* __restrict__ z, int64_t n,
-                                                    int64_t ld, float* __restrict__ zinv,
+__device__ __forceinline__ void inv_det_vec4_queued(const float* z, int64_t n,
+                                                    int64_t ld, float* zinv,
                                                     float* __restrict__ det, float tau,
                                                     uint8_t* __restrict__ status,
                                                     unsigned long long* __restrict__ counts) {
@@ -214,7 +220,7 @@ __device__ __forceinline__ void inv_det_vec4_queued(const float* __restrict__ z,
 
 template <int ALG, bool STAT>
 __global__ void __launch_bounds__(kThreads)
-    k_inv_det_vec4(const float* __restrict__ z, int64_t n, int64_t ld, float* __restrict__ zinv,
+    k_inv_det_vec4(const float* z, int64_t n, int64_t ld, float* zinv,
                    float* __restrict__ det, float tau, uint8_t* __restrict__ status,
                    unsigned long long* __restrict__ counts) {
   inv_det_vec4<ALG, STAT>(z, n, ld, zinv, det, tau, status, counts);
@@ -224,15 +230,15 @@ __global__ void __launch_bounds__(kThreads)
 // otherwise cost the FP32 streaming pass a block).
 template <int ALG, bool STAT>
 __global__ void __launch_bounds__(kThreads, 3)
-    k_inv_det_vec4_f64(const float* __restrict__ z, int64_t n, int64_t ld,
-                       float* __restrict__ zinv, float* __restrict__ det, float tau,
+    k_inv_det_vec4_f64(const float* z, int64_t n, int64_t ld,
+                       float* zinv, float* __restrict__ det, float tau,
                        uint8_t* __restrict__ status, unsigned long long* __restrict__ counts) {
   inv_det_vec4_queued<ALG, STAT>(z, n, ld, zinv, det, tau, status, counts);
 }
 
 template <int ALG, bool STAT>
 __global__ void __launch_bounds__(kThreads)
-    k_inv_det_scalar(const float* __restrict__ z, int64_t n, int64_t ld, float* __restrict__ zinv,
+    k_inv_det_scalar(const float* z, int64_t n, int64_t ld, float* zinv,
                      float* __restrict__ det, float tau, uint8_t* __restrict__ status,
                      unsigned long long* __restrict__ counts) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;

@@ -97,12 +97,31 @@ extern "C" int zinv_det_host(const float* z_host, int64_t n, int64_t ld, float* 
   const size_t sb = slot_bytes(chunk);
   char* ws = static_cast<char*>(d_ws);
 
-#define ZCHK(x)                                 \
-  do {                                          \
-    if ((x) != cudaSuccess) {                   \
-      cudaGetLastError();                       \
-      return ZINV_ERR_LAUNCH;                   \
-    }                                           \
+  // Once the first copy is queued, every way out -- success or error -- records
+  // the three streams' ends and makes the caller's stream wait for them, so
+  // a caller that sees an error and synchronizes its stream before freeing the
+  // host buffers never races with a transfer still in flight.
+  bool enqueued = false;
+  auto join = [&]() {
+    bool ok = true;
+    for (int i = 0; i < 3; ++i) {
+      ok = ok && cudaEventRecord(p.done[i], p.st[i]) == cudaSuccess;
+      ok = ok && cudaStreamWaitEvent(user, p.done[i], 0) == cudaSuccess;
+    }
+    return ok;
+  };
+  auto fail = [&](int code) {
+    cudaGetLastError();
+    if (enqueued && !join()) {
+      // the join itself failed: wait on the host so nothing is left in flight
+      for (auto& st : p.st) cudaStreamSynchronize(st);
+      cudaGetLastError();
+    }
+    return code;
+  };
+#define ZCHK(x)                                   \
+  do {                                            \
+    if ((x) != cudaSuccess) return fail(ZINV_ERR_LAUNCH); \
   } while (0)
 
   ZCHK(cudaEventRecord(p.start, user));
@@ -116,6 +135,7 @@ extern "C" int zinv_det_host(const float* z_host, int64_t n, int64_t ld, float* 
     float* dd = reinterpret_cast<float*>(ws + slot * sb + round_up((size_t)chunk * 9 * 4));
     // copy in (after the slot's previous chunk has drained)
     if (c >= kSlots) ZCHK(cudaStreamWaitEvent(p.st[0], p.drained[slot], 0));
+    enqueued = true;
     for (int k = 0; k < 9; ++k)
       ZCHK(cudaMemcpyAsync(dz + k * chunk, z_host + k * ld + p0, (size_t)m * 4,
                            cudaMemcpyHostToDevice, p.st[0]));
@@ -123,7 +143,7 @@ extern "C" int zinv_det_host(const float* z_host, int64_t n, int64_t ld, float* 
     // compute in place
     ZCHK(cudaStreamWaitEvent(p.st[1], p.in_ready[slot], 0));
     rc = inv_det_entry(alg, dz, m, chunk, dz, dd, tau, nullptr, nullptr, p.st[1]);
-    if (rc != ZINV_OK) return rc;
+    if (rc != ZINV_OK) return fail(rc);
     ZCHK(cudaEventRecord(p.computed[slot], p.st[1]));
     // copy out
     ZCHK(cudaStreamWaitEvent(p.st[2], p.computed[slot], 0));
@@ -133,10 +153,7 @@ extern "C" int zinv_det_host(const float* z_host, int64_t n, int64_t ld, float* 
     ZCHK(cudaMemcpyAsync(det_host + p0, dd, (size_t)m * 4, cudaMemcpyDeviceToHost, p.st[2]));
     ZCHK(cudaEventRecord(p.drained[slot], p.st[2]));
   }
-  for (int i = 0; i < 3; ++i) {
-    ZCHK(cudaEventRecord(p.done[i], p.st[i]));
-    ZCHK(cudaStreamWaitEvent(user, p.done[i], 0));
-  }
+  if (!join()) return fail(ZINV_ERR_LAUNCH);
 #undef ZCHK
   return ZINV_OK;
 }

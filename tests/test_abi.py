@@ -33,6 +33,17 @@ def test_library_exports_every_declared_symbol():
     assert "argument" in zp.status_string(-1)
 
 
+def test_binding_declares_every_entry_point():
+    """load() gives every declared entry point that takes arguments a ctypes
+    signature, so no call goes out with ctypes' default int conversions (which
+    would truncate 64-bit sizes and pointers)."""
+    import paper_1807_08084_gb300 as zp
+    lib = zp.load()
+    undeclared = [n for h in sorted((ROOT / "include").glob("*.h")) for n in declared(h)
+                  if n != "zinv_abi_version" and getattr(lib, n).argtypes is None]
+    assert not undeclared, f"no argtypes for: {undeclared}"
+
+
 def test_synth_library_loads():
     from paper_1807_08084_gb300.synth import gpu
     lib = gpu.load()
