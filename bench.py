@@ -43,6 +43,7 @@ UNIT = "Gmatrices/s"
 BYTES_FWD = 76     # 9 planes in + 9 planes + det out, FP32
 BYTES_BWD = 116    # W, det, g_W, g_det in; g_Z out
 L2_BYTES = 126 * 2**20  # GB300 L2
+HBM_SPEC_GBS = 7900.0  # GB300 nominal HBM3e bandwidth (context beside the measured copy)
 
 
 def peaks():
@@ -51,6 +52,22 @@ def peaks():
         d = json.loads(p.read_text())
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def sm_max_mhz() -> float:
+    """Maximum SM clock: the measured figure if present, else nvidia-smi."""
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        if d.get("sm_max_mhz"):
+            return float(d["sm_max_mhz"])
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(torch.cuda.current_device()),
+                              "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=10).stdout
+        return float(out.strip().splitlines()[0])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return 2070.0
 
 
 def source_hash(files) -> str:
@@ -239,30 +256,77 @@ def host_cpu() -> str:
     return f"{model}, {os.cpu_count()} cores"
 
 
-def cpu_oracle_baseline(z_dev: torch.Tensor, budget_s: float = 12.0):
-    """The FP64 oracle on the host cores, on the first pixels of the same image,
-    chunk after chunk until ~budget_s of oracle time."""
-    import oracle
-    o = oracle.load()
-    zf = z_dev.reshape(9, -1)
-    chunk = 1 << 21
-    done, spent, p0 = 0, 0.0, 0
-    while spent < budget_s and p0 < zf.shape[1]:
-        zc = zf[:, p0:p0 + chunk].cpu().numpy()
-        t = time.perf_counter()
-        o.zinv_det(zc)
-        spent += time.perf_counter() - t
-        done += zc.shape[1]
-        p0 += chunk
-    return {"value": done / spent / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "host": host_cpu(),
-            "sample": f"first {done} matrices of the same image, FP64 Gauss-Jordan "
-                      f"inverse and det, single thread ({spent:.1f} s)"}
+def _pool_rate(route, data, workers, budget_s, share=True):
+    """Items per second of the oracle over `workers` processes: whole steps
+    (every worker once over its data) until budget_s of wall time."""
+    from oracle.pool import OraclePool
+    with OraclePool(route, data, workers, share=share) as pool:
+        pool.step()  # warm-up: page in the data and the code
+        items, wall = 0, 0.0
+        while wall < budget_s:
+            it, t, _ = pool.step()
+            items += it
+            wall += t
+    return items / wall, pool.n
+
+
+def cpu_oracle_baseline(images: dict, budget_s: float = 2.0):
+    """The unmodified FP64 oracle on the host cores: one thread, and one process
+    per core on disjoint shares of the data (oracle.pool), for the Gauss-Jordan
+    and the cofactor (adjugate) routes on samples of the 16384 x 16384 and the
+    cond-controlled 4096 x 4096 images, and the Wishart forward + backward on a
+    band of rows of the 4096 x 4096 pair.  The headline value is the
+    Gauss-Jordan route on all cores on the 16384 x 16384 sample."""
+    import tempfile
+    cores = os.cpu_count() or 1
+    per_worker = 1 << 19
+    out = {"host": host_cpu(), "routes": {}}
+    with tempfile.TemporaryDirectory() as d:
+        for key, z_dev in (("scale_16k", images["scale_16k"]),
+                           ("precision_4k", images["precision_4k"])):
+            zf = z_dev.reshape(9, -1)
+            m_all = min(zf.shape[1], cores * per_worker)
+            all_path, one_path = f"{d}/{key}_all.npy", f"{d}/{key}_one.npy"
+            np.save(all_path, zf[:, :m_all].cpu().numpy())
+            np.save(one_path, zf[:, :2 * per_worker].cpu().numpy())
+            for route in ("ge", "adj"):
+                r1, _ = _pool_rate(route, one_path, 1, budget_s)
+                rn, used = _pool_rate(route, all_path, cores, budget_s)
+                out["routes"][f"{key}/{route}"] = {
+                    "gmat_s_1_thread": r1 / 1e9, "gmat_s_all_cores": rn / 1e9, "cores": used,
+                    "matrices_all_cores": m_all, "matrices_1_thread": 2 * per_worker}
+        s1, s2 = images["wishart_pair_4k"]
+        rows_per = 32
+        rows_all = min(s1.shape[1], cores * rows_per)
+        paths = {}
+        for name, rows in (("one", rows_per), ("all", rows_all)):
+            pa, pb = f"{d}/w1_{name}.npy", f"{d}/w2_{name}.npy"
+            np.save(pa, s1[:, :rows].cpu().numpy())
+            np.save(pb, s2[:, :rows].cpu().numpy())
+            paths[name] = (pa, pb)
+        r1, _ = _pool_rate("wishart", paths["one"], 1, budget_s)
+        rn, used = _pool_rate("wishart", paths["all"], cores, budget_s)
+        out["routes"]["wishart_pair_4k/fwd+bwd"] = {
+            "gpix_s_1_thread": r1 / 1e9, "gpix_s_all_cores": rn / 1e9, "cores": used,
+            "sample": f"the first {rows_all} rows of both 4096-wide dates, 7 x 7 uniform taps, "
+                      f"{rows_all // used} output rows per process (forward over the band "
+                      "plus its 3-row halo, backward over the band)"}
+    head = out["routes"]["scale_16k/ge"]
+    return {"value": head["gmat_s_all_cores"], "unit": UNIT, "cores": head["cores"],
+            "kind": "oracle",
+            "sample": f"the first {head['matrices_all_cores']} matrices of the same 16384 x 16384 "
+                      f"image, one process per core ({head['matrices_all_cores'] // head['cores']} "
+                      "matrices each), FP64 Gauss-Jordan inverse and det of the oracle as it "
+                      f"stands, repeated for ~{budget_s:.0f} s",
+            "single_thread": head["gmat_s_1_thread"], **out}
 
 
 def fp32_peak_tflops() -> float:
-    """FP32 FMA peak of a GB300: 152 SMs x 128 lanes x 2 flops x 2.07 GHz."""
-    return 152 * 128 * 2 * 2.07e9 / 1e12
+    """FP32 FMA peak of this GPU: SMs (read from the device) x 128 FP32 lanes x
+    2 flops x the maximum SM clock (152 x 128 x 2 x 2.07 GHz = 80.5 TFLOP/s on
+    a GB300)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 128 * 2 * sm_max_mhz() * 1e6 / 1e12
 
 
 def workload_config(H: int, W: int, world: int) -> dict:
@@ -276,32 +340,40 @@ def workload_config(H: int, W: int, world: int) -> dict:
 
 
 def run_reference(args, world, rank):
-    """The FP64 oracle timed on the host cores (the reference arm)."""
+    """The FP64 oracle timed on the host cores (the reference arm): one process
+    per core, each running the unmodified oracle over the same seeded sample of
+    the workload every step."""
     if rank != 0:
         return
-    import oracle
+    import tempfile
+    from oracle.pool import OraclePool
     from paper_1807_08084_gb300 import synth as S
     w = S.WORKLOADS["scale_16k"]
-    o = oracle.load()
     m = 1 << 18
     z = w.packed_z(np.arange(m, dtype=np.uint64))   # numpy twin, CPU only
-    for _ in range(args.warmup):
-        o.zinv_det(z)
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        o.zinv_det(z)
-    dt = (time.perf_counter() - t) / args.steps
-    value = m / dt / 1e9
+    with tempfile.TemporaryDirectory() as d:
+        path = f"{d}/sample.npy"
+        np.save(path, z)
+        with OraclePool("ge", path, share=False) as pool:
+            for _ in range(args.warmup):
+                pool.step()
+            items, wall = 0, 0.0
+            for _ in range(args.steps):
+                it, t, _ = pool.step()
+                items += it
+                wall += t
+            cores = pool.n
+    value = items / wall / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": workload_config(w.H, w.W, world),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "host": host_cpu(),
-                             "sample": f"the first {m} matrices of the {w.H}x{w.W} image per "
-                                       "step, FP64 Gauss-Jordan inverse and det, single "
-                                       "thread"},
+                             "sample": f"per step, each of {cores} processes (one per core) "
+                                       f"runs the oracle's FP64 Gauss-Jordan inverse and det "
+                                       f"over the first {m} matrices of the {w.H}x{w.W} image"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -326,6 +398,10 @@ def main():
     ap.add_argument("--paper", type=int, default=1,
                     help="also time the paper's own workload sizes (its Table 2)")
     ap.add_argument("--ws-rows", type=int, default=4096, help="Wishart image height")
+    ap.add_argument("--plain256", type=int, default=1,
+                    help="also time single launches on the 256 x 256 latency workload")
+    ap.add_argument("--cpu-baseline", type=int, default=1,
+                    help="time the FP64 oracle on the host cores (rank 0, one GPU only)")
     ap.add_argument("--rows", type=int, default=16384,
                     help="image height (16384 = the full workload; smaller for profiling)")
     args = ap.parse_args()
@@ -368,7 +444,7 @@ def main():
     def path(ms_):
         gbs = BYTES_FWD * n / (ms_ * 1e-3) / 1e9
         return {"gmat_s": n / (ms_ * 1e-3) / 1e9, "ms": ms_, "gbs": gbs,
-                "frac_hbm": gbs / hbm_peak}
+                "frac_hbm": gbs / hbm_peak, "frac_hbm_spec": gbs / HBM_SPEC_GBS}
 
     paths = {"adjugate": path(ms)}
     sub = args.sub_steps
@@ -406,6 +482,29 @@ def main():
         paths[key]["dram_bytes_ncu"] = None if t is None else t * scale
     del g_w, g_det, g_z
     sampler.stop()
+
+    cpu_inputs = {"scale_16k": z}  # device images the host-core oracle timing samples
+
+    # --- plain_256 (256 x 256, N = 4 looks of one fixed Sigma): launch latency --
+    plain256 = {}
+    if args.plain256:
+        wq = S.WORKLOADS["plain_256"]
+        zq = G.packed_z(wq)
+        zqi = torch.empty_like(zq)
+        dq = torch.empty((wq.H, wq.W), device="cuda")
+        t_a = timed_device(lambda: zp.zinv_det(zq, zp.PLAIN, out=(zqi, dq)), sub, args.warmup,
+                           world)
+        t_c = timed_device(lambda: zp.chol_zinv_det(zq, out=(zqi, dq)), sub, args.warmup, world)
+        t_b = timed(lambda: zp.zinv_det(zq, zp.PLAIN, out=(zqi, dq)), 10 * sub, args.warmup,
+                    world)
+        plain256 = {"matrices": wq.n, "adjugate_us": t_a * 1e3, "cholesky_us": t_c * 1e3,
+                    "adjugate_back_to_back_us": t_b * 1e3,
+                    "adjugate_back_to_back_gmat_s": wq.n / (t_b * 1e-3) / 1e9,
+                    "l2": "L2-resident (5.0 MB per launch): no flush; *_us are the median device "
+                          "time of single launches, back_to_back the mean of consecutive ones",
+                    "workload": "256x256 packed Z, N = 4 looks of the fixed Sigma "
+                                "(Bartlett-sampled complex Wishart)"}
+        del zq, zqi, dq
 
     # --- fused multilook (8192 x 8192 single-look, boxcar 3/5/7) ---------------
     multilook = {}
@@ -467,7 +566,8 @@ def main():
         precision["flagged_fraction"] = int(cnt[1]) / wp.n
         precision["workload"] = ("4096x4096 packed Z = U diag(1, k^-v, 1/k) U^H, k log-uniform "
                                  "in [1, 1e7], tau = 2^-10")
-        del zp4, zi4, d4
+        cpu_inputs["precision_4k"] = zp4
+        del zi4, d4
 
     # --- the paper's own workload sizes (its Table 2): context, not the headline --
     paper = {}
@@ -533,7 +633,9 @@ def main():
                              "frac_alu": tf / alu_peak,
                              "gbs": 48 * ww.n / (t * 1e-3) / 1e9}
         wishart["alu_peak_tflops"] = alu_peak
-        del s1, s2, ws_buf
+        if ww.H == 4096:
+            cpu_inputs["wishart_pair_4k"] = (s1, s2)
+        del ws_buf
 
     # --- end to end through the host-buffer entry point -----------------------
     e2e = None
@@ -559,7 +661,15 @@ def main():
                                  "through device memory, 3 streams)"}}
         del z_host, zinv_h, det_h, ws
 
-    cpu = cpu_oracle_baseline(z) if (rank == 0 and world == 1) else None
+    cpu = None
+    if args.cpu_baseline and rank == 0 and world == 1:
+        if "precision_4k" not in cpu_inputs:
+            cpu_inputs["precision_4k"] = G.packed_z(S.WORKLOADS["precision_4k"])
+        if "wishart_pair_4k" not in cpu_inputs:
+            wpair = S.WORKLOADS["wishart_pair_4k"]
+            cpu_inputs["wishart_pair_4k"] = (G.image(wpair, 0), G.image(wpair, 1))
+        cpu = cpu_oracle_baseline(cpu_inputs)
+    del cpu_inputs
     traffic = traffic_record("zinv_det_plain_vec4")
     if traffic is not None:
         traffic *= n / float(1 << 28)
@@ -574,9 +684,16 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak,
                          "traffic": traffic, "peak_kind": peak_kind,
+                         "peak_spec": HBM_SPEC_GBS, "frac_spec": achieved / HBM_SPEC_GBS,
+                         "note": "peak/frac: the measured HBM copy (MEASURED_PEAKS.json); "
+                                 "peak_spec/frac_spec: the GB300 nominal HBM3e bandwidth",
                          "kernel": "k_inv_det_vec4<plain>",
                          "algorithmic_bytes_per_launch": BYTES_FWD * n},
+            "tolerance_note": "plain FP32 (the headline kernel) meets 1e-5 cond on the plain_256 "
+                              "and scale_16k workloads; on the cond-controlled precision_4k "
+                              "workload (cond up to 1e7) it needs COMPENSATED or FP64_RECOMPUTE",
             "paths": paths,
+            "plain_256": plain256 or None,
             "multilook_8k": multilook or None,
             "wishart_pair_4k": wishart or None,
             "nlm_23x23": nlm or None,

@@ -150,3 +150,27 @@ def test_full_size_pair(zlib, orc):
         rq = rq.reshape(cy1 - cy0, cx1 - cx0)[y0 - cy0:y1 - cy0, x0 - cx0:x1 - cx0]
         gq = q[y0:y1, x0:x1].cpu().numpy()
         assert np.abs(gq - rq).max() <= Q_ABS
+
+
+def test_full_size_gradient_and_loss_vs_oracle(zlib, tmp_path):
+    """The 4096 x 4096 pair in the benchmark's launch configuration: the weight
+    gradient after the 32,768-tile fixed-order reduction, and the loss, against
+    the FP64 oracle over the full image (row bands on all host cores)."""
+    from oracle_bands import wishart_by_bands
+    from paper_1807_08084_gb300.synth import gpu as G
+    w = S.WORKLOADS["wishart_pair_4k"]
+    s1, s2 = G.image(w, 0), G.image(w, 1)
+    wt = weights(7, seed=9)
+    wd = torch.from_numpy(wt).cuda()
+    loss = zlib.wishart_stat_fwd(s1, s2, wd, 7)
+    g = zlib.wishart_stat_bwd(s1, s2, wd, 7)
+    torch.cuda.synchronize()
+    p1, p2 = tmp_path / "s1.npy", tmp_path / "s2.npy"
+    np.save(p1, s1.cpu().numpy())
+    np.save(p2, s2.cpu().numpy())
+    del s1, s2
+    ref_loss, ref_g = wishart_by_bands(str(p1), str(p2), w.H, 7, wt)
+    gg = g.cpu().numpy().astype(np.float64)
+    err = np.abs(gg - ref_g).max() / np.abs(ref_g).max()
+    assert err <= G_REL, f"grad rel err {err:.3e}"
+    assert abs(float(loss) - ref_loss) <= Q_ABS * w.H * w.W, (float(loss), ref_loss)

@@ -410,3 +410,25 @@ def test_mutants_are_caught(mutant):
         except (AssertionError, FloatingPointError, ValueError):
             failed.append(check.__name__)
     assert failed, f"no pin catches mutant {mutant}: {MUTANTS[mutant]}"
+
+
+def test_row_bands_reproduce_the_full_image_oracle(orc):
+    """The banded evaluation the full-size GPU test uses (sub-images with r halo
+    rows, cut at the border) gives the full-image oracle's loss and weight
+    gradient: a halo or band-offset slip would change both."""
+    from oracle_bands import wishart_by_bands
+    from paper_1807_08084_gb300 import synth as S
+    import tempfile
+    import os
+    w = S.scaled(S.WORKLOADS["wishart_pair_4k"], 37, 29)
+    s1, s2 = w.image(0), w.image(1)
+    wt = np.random.default_rng(4).uniform(0.5, 1.5, 25) / 25
+    with tempfile.TemporaryDirectory() as d:
+        p1, p2 = os.path.join(d, "a.npy"), os.path.join(d, "b.npy")
+        np.save(p1, s1)
+        np.save(p2, s2)
+        loss, grad = wishart_by_bands(p1, p2, w.H, 5, wt, band_rows=6, processes=2)
+    ref_loss = orc.wishart_fwd(s1, s2, 5, wt)
+    ref_grad = orc.wishart_bwd(s1, s2, 5, wt, 1.0)
+    assert abs(loss - ref_loss) <= 1e-12 * abs(ref_loss) * 37
+    np.testing.assert_allclose(grad, ref_grad, rtol=1e-12, atol=1e-12 * np.abs(ref_grad).max())
