@@ -6,15 +6,24 @@
 // w_ij = exp(-L d(i, j) / h) over the in-image neighbours within the search
 // radius, and Z'_i = sum_j w_ij Z_j / sum_j w_ij.
 //
-// The per-pixel log-dets are formed once per staged pixel (compensated route);
-// the per-pair determinant -- 529 per pixel for a 23 x 23 window -- is the hot
-// arithmetic.  It is computed either by Algorithm 2's cofactor expansion
-// (Eq. adjoint_elements, Eq. detr: no division, no square root) or by
-// Algorithm 1's Cholesky route (three square roots, two reciprocals), so the
-// two can be compared where arithmetic, not memory, sets the time.
+// In base 2, with D_ij = det(Z_i + Z_j) and h_i = log2(det Z_i) / 2:
+//     w_ij = 2^(-p t_ij),  t_ij = max(log2 D_ij - (3 + h_i) - h_j, 0),  p = L / h,
+// (det((Z_i + Z_j)/2) = D_ij / 8 for 3x3 matrices; t >= 0 in exact arithmetic,
+// the clamp absorbs rounding).  h_i is formed once per staged pixel (compensated
+// route); per pair the work is D_ij -- 529 determinants per pixel for a 23 x 23
+// window -- one log2 and one exp2.  D_ij is computed either by Algorithm 2's
+// cofactor expansion (Eq. adjoint_elements, Eq. detr: no division, no square
+// root) or by Algorithm 1's Cholesky route (three square roots, two
+// reciprocals); everything else is shared, so the two can be compared where
+// arithmetic, not memory, sets the time.
 //
-// Tiles of 32 x 8 outputs, one thread per output; the tile plus a halo of the
-// search radius (Z and its log-det) sits in shared memory, rows warp-contiguous.
+// Tiles of 32 x 16 outputs, 256 threads; each thread owns two vertically
+// adjacent outputs A and B, held as the two halves of packed f32x2 values:
+// every neighbour Z_j loaded from shared memory serves both outputs' pairs
+// (one packed sum Z_A + Z_j | Z_B + Z_j, one packed determinant by Algorithm 2,
+// one packed weighted accumulation).  The rows of the two windows are walked
+// together; a row outside one output's window gets weight 0 for that output.
+// The tile plus a halo of the search radius (Z and h) sits in shared memory.
 #include "common.cuh"
 #include "pixel.cuh"
 
@@ -23,13 +32,13 @@ namespace {
 
 constexpr int kNT = 256;
 constexpr int kNW = 32;  // tile width
-constexpr int kNH = 8;   // tile height
+constexpr int kNH = 16;  // tile height: 8 row pairs
 
 struct NlmArgs {
   const float* z;
   int64_t H, W, ld;
   int radius;
-  float c;  // -L / (h ln 2): w = 2^(c d)
+  float p;  // L / h
   float* out;
 };
 
@@ -48,21 +57,21 @@ __device__ __forceinline__ float det_cholesky(const float x[9]) {
   const float l21r = (er - (l20r * l10r + l20i * l10i)) * v1;
   const float l21i = (-ei - (l20i * l10r - l20r * l10i)) * v1;
   const float l22 = __fsqrt_rn(f - (l20r * l20r + l20i * l20i) - (l21r * l21r + l21i * l21i));
-  const float p = l00 * l11 * l22;
-  return p * p;
+  const float q = l00 * l11 * l22;
+  return q * q;
 }
 
 template <int METHOD, int RAD>
-__global__ void __launch_bounds__(kNT) k_nlm(NlmArgs a) {
+__global__ void __launch_bounds__(kNT, 2) k_nlm(NlmArgs a) {
   constexpr int SW = kNW + 2 * RAD, SH = kNH + 2 * RAD;
   extern __shared__ __align__(16) float smem[];
-  float* Zs = smem;                   // [9][SH][SW]
-  float* Ls = smem + 9 * SH * SW;     // [SH][SW] log-dets
+  float* Zs = smem;                // [9][SH][SW]
+  float* Hs = smem + 9 * SH * SW;  // [SH][SW] half log2-dets
   const int64_t n = a.H * a.W;
   const int64_t tiles_x = (a.W + kNW - 1) / kNW;
   const int64_t tiles = tiles_x * ((a.H + kNH - 1) / kNH);
-  const int tx = threadIdx.x % kNW, ty = threadIdx.x / kNW;
-  const float three_ln2 = 2.0794415416798357f;
+  const int tx = threadIdx.x % kNW, ty = 2 * (threadIdx.x / kNW);
+  const float inv_ln2 = 1.44269504088896340736f;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int64_t y0 = (t / tiles_x) * kNH, x0 = (t % tiles_x) * kNW;
     __syncthreads();
@@ -70,114 +79,80 @@ __global__ void __launch_bounds__(kNT) k_nlm(NlmArgs a) {
       const int sy = i / SW, sx = i - (i / SW) * SW;
       const int64_t gy = y0 - RAD + sy, gx = x0 - RAD + sx;
       if (gy < 0 || gy >= a.H || gx < 0 || gx >= a.W) continue;  // never read
-      const int64_t p = gy * a.W + gx;
+      const int64_t q = gy * a.W + gx;
       float v[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        v[c] = __ldg(a.z + c * a.ld + p);
+        v[c] = __ldg(a.z + c * a.ld + q);
         Zs[(c * SH + sy) * SW + sx] = v[c];
       }
       const dd<float> dt = det_comp<float>(v);
-      Ls[sy * SW + sx] = logf(dt.hi) + dt.lo / dt.hi;
+      Hs[sy * SW + sx] = 0.5f * (log2f(dt.hi) + (dt.lo / dt.hi) * inv_ln2);
     }
     __syncthreads();
-    const int64_t gy = y0 + ty, gx = x0 + tx;
-    if (gy >= a.H || gx >= a.W) continue;
-    const int cy = ty + RAD, cx = tx + RAD;
-    float zi[9];
+    const int64_t gyA = y0 + ty, gx = x0 + tx;
+    if (gyA >= a.H || gx >= a.W) continue;
+    const bool hasB = gyA + 1 < a.H;
+    const int cy = ty + RAD, cx = tx + RAD;  // shared-memory position of output A
+    float2 zi[9], acc[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) zi[c] = Zs[(c * SH + cy) * SW + cx];
-    const float li = Ls[cy * SW + cx];
-    // in-image part of the search window
-    const int dy0 = (int)(gy - RAD < 0 ? -gy : -RAD);
-    const int dy1 = (int)(gy + RAD >= a.H ? a.H - 1 - gy : RAD);
+    for (int c = 0; c < 9; ++c) {
+      const float za = Zs[(c * SH + cy) * SW + cx];
+      zi[c] = make_float2(za, hasB ? Zs[(c * SH + cy + 1) * SW + cx] : za);
+      acc[c] = make_float2(0.0f, 0.0f);
+    }
+    const float kA = 3.0f + Hs[cy * SW + cx];
+    const float kB = hasB ? 3.0f + Hs[(cy + 1) * SW + cx] : kA;
+    // in-image rows of the two windows (B's starts one row later) and columns
+    const int64_t a_lo = gyA - RAD < 0 ? 0 : gyA - RAD;
+    const int64_t a_hi = gyA + RAD >= a.H ? a.H - 1 : gyA + RAD;
+    const int64_t b_lo = gyA + 1 - RAD < 0 ? 0 : gyA + 1 - RAD;
+    const int64_t b_hi = hasB ? (gyA + 1 + RAD >= a.H ? a.H - 1 : gyA + 1 + RAD) : a_hi;
     const int dx0 = (int)(gx - RAD < 0 ? -gx : -RAD);
     const int dx1 = (int)(gx + RAD >= a.W ? a.W - 1 - gx : RAD);
-    float out[9], wsum;
-    if constexpr (METHOD == 0) {
-      // Algorithm 2: neighbours two at a time (dx, dx + 1); the sums, the pair
-      // determinants and the weighted accumulation run on packed float2 pairs
-      // (f32x2, each half rounded as the scalar operation), the logs and exp2s
-      // stay scalar; even and odd neighbours accumulate in the two halves.
-      float2 zi2[9], acc[9];
+    const float np = -a.p;
+    float2 ws = make_float2(0.0f, 0.0f);
+    for (int64_t gy = a_lo; gy <= b_hi; ++gy) {
+      const float2 m = make_float2(gy <= a_hi ? 1.0f : 0.0f, hasB && gy >= b_lo ? 1.0f : 0.0f);
+      const int srow = (int)(gy - y0) + RAD;
+      const float* zrow = Zs + srow * SW + cx;
+      const float* hrow = Hs + srow * SW + cx;
+      for (int dx = dx0; dx <= dx1; ++dx) {
+        float zj[9];
+        float2 zs[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        zi2[c] = make_float2(zi[c], zi[c]);
-        acc[c] = make_float2(0.0f, 0.0f);
-      }
-      float2 ws = make_float2(0.0f, 0.0f);
-      for (int dy = dy0; dy <= dy1; ++dy) {
-        const int row = cy + dy;
-        const float* lrow = Ls + row * SW + cx;
-        int dx = dx0;
-        for (; dx < dx1; dx += 2) {
-          const int col = cx + dx;
-          float2 zj[9], zs[9];
-#pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            const float* q = Zs + (c * SH + row) * SW + col;
-            zj[c] = make_float2(q[0], q[1]);
-            zs[c] = add_rn(zi2[c], zj[c]);
-          }
-          const float2 det = det_adjugate<float2>(zs);
-          // ln det((Zi+Zj)/2) = ln det(Zi+Zj) - 3 ln 2
-          const float d0 = (logf(det.x) - three_ln2) - 0.5f * (li + lrow[dx]);
-          const float d1 = (logf(det.y) - three_ln2) - 0.5f * (li + lrow[dx + 1]);
-          const float2 w =
-              make_float2(exp2f(a.c * fmaxf(d0, 0.0f)), exp2f(a.c * fmaxf(d1, 0.0f)));
-#pragma unroll
-          for (int c = 0; c < 9; ++c) acc[c] = fma_rn(w, zj[c], acc[c]);
-          ws = add_rn(ws, w);
+        for (int c = 0; c < 9; ++c) {
+          zj[c] = zrow[c * SH * SW + dx];
+          zs[c] = add_rn(zi[c], make_float2(zj[c], zj[c]));
         }
-        if (dx == dx1) {  // an odd count leaves one neighbour: the first halves
-          const int col = cx + dx;
-          float zj[9], zs[9];
+        float2 D;
+        if constexpr (METHOD == 0) {
+          D = det_adjugate<float2>(zs);
+        } else {
+          float xa[9], xb[9];
 #pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            zj[c] = Zs[(c * SH + row) * SW + col];
-            zs[c] = add_rn(zi[c], zj[c]);
-          }
-          const float det = det_adjugate<float>(zs);
-          const float d0 = (logf(det) - three_ln2) - 0.5f * (li + lrow[dx]);
-          const float w = exp2f(a.c * fmaxf(d0, 0.0f));
-#pragma unroll
-          for (int c = 0; c < 9; ++c) acc[c].x = fmaf(w, zj[c], acc[c].x);
-          ws.x += w;
+          for (int c = 0; c < 9; ++c) xa[c] = zs[c].x, xb[c] = zs[c].y;
+          D = make_float2(det_cholesky(xa), det_cholesky(xb));
         }
-      }
+        const float hj = hrow[dx];
+        const float ta = __log2f(D.x) - (kA + hj);
+        const float tb = __log2f(D.y) - (kB + hj);
+        const float2 w = mul_rn(make_float2(exp2f(np * fmaxf(ta, 0.0f)),
+                                            exp2f(np * fmaxf(tb, 0.0f))), m);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) out[c] = acc[c].x + acc[c].y;
-      wsum = ws.x + ws.y;
-    } else {
-      // Algorithm 1: one neighbour at a time (pairing its scalar square roots
-      // and reciprocals only cost it registers)
-#pragma unroll
-      for (int c = 0; c < 9; ++c) out[c] = 0.0f;
-      wsum = 0.0f;
-      for (int dy = dy0; dy <= dy1; ++dy) {
-        const int row = cy + dy;
-        for (int dx = dx0; dx <= dx1; ++dx) {
-          const int col = cx + dx;
-          float zj[9], zs[9];
-#pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            zj[c] = Zs[(c * SH + row) * SW + col];
-            zs[c] = zi[c] + zj[c];
-          }
-          const float det = det_cholesky(zs);
-          // ln det((Zi+Zj)/2) = ln det(Zi+Zj) - 3 ln 2
-          const float dist = (logf(det) - three_ln2) - 0.5f * (li + Ls[row * SW + col]);
-          const float w = exp2f(a.c * fmaxf(dist, 0.0f));
-#pragma unroll
-          for (int c = 0; c < 9; ++c) out[c] = fmaf(w, zj[c], out[c]);
-          wsum += w;
-        }
+        for (int c = 0; c < 9; ++c) acc[c] = fma_rn(w, make_float2(zj[c], zj[c]), acc[c]);
+        ws = add_rn(ws, w);
       }
     }
-    const float inv = 1.0f / wsum;
-    const int64_t p = gy * a.W + gx;
+    const int64_t q = gyA * a.W + gx;
+    const float ia = 1.0f / ws.x;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) a.out[c * n + p] = out[c] * inv;
+    for (int c = 0; c < 9; ++c) a.out[c * n + q] = acc[c].x * ia;
+    if (hasB) {
+      const float ib = 1.0f / ws.y;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) a.out[c * n + q + a.W] = acc[c].y * ib;
+    }
   }
 }
 
@@ -228,7 +203,7 @@ extern "C" int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int
   int rc = device_info(&di);
   if (rc != ZINV_OK) return rc;
   if (!device_accessible(z) || !device_accessible(z_out)) return ZINV_ERR_ARG;
-  NlmArgs a{z, H, W, ld, radius, -looks / (h * 0.69314718055994531f), z_out};
+  NlmArgs a{z, H, W, ld, radius, looks / h, z_out};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return method == 0 ? dispatch_nlm<0>(a, s) : dispatch_nlm<1>(a, s);
 }
