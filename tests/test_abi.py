@@ -8,7 +8,7 @@ from pathlib import Path
 import pytest
 
 ROOT = Path(__file__).resolve().parents[1]
-DECL = re.compile(r"^\s*(?:int|size_t|const\s+char\s*\*)\s+(\w+)\s*\(", re.M)
+DECL = re.compile(r"^\s*(?:int64_t|int|size_t|const\s+char\s*\*)\s+(\w+)\s*\(", re.M)
 
 
 def declared(header: Path):

@@ -193,3 +193,25 @@ def test_full_size_crops(zlib, orc):
             dc = det[cy0:cy1, cx0:cx1].reshape(-1)
             check(zc, dc, ref, "plain_fp64", sel=sel)
         del zinv, det
+
+
+@pytest.mark.parametrize("win", [3, 7])
+@pytest.mark.parametrize("mode", ["plain", "compensated_fp64"])
+def test_weighted_larger_ragged_image(zlib, orc, win, mode):
+    """An 811 x 1000 image: 1632 tiles of 32 x 16 with ragged right and bottom
+    tiles.  Every pixel against the oracle, the status plane against the
+    counters, and the same bits on a repeat."""
+    H, W = 811, 1000
+    w = S.scaled(S.WORKLOADS["wishart_pair_4k"], H, W)
+    s_np = w.image(1)
+    wts = np.random.default_rng(40 + win).uniform(0.2, 1.0, win * win).astype(np.float32)
+    s = torch.from_numpy(s_np).cuda()
+    wt = torch.from_numpy(wts).cuda()
+    zinv, det, st, cnt = zlib.multilook_zinv_det(s, win, wt, MODES[mode], want_status=True,
+                                                 want_counts=True)
+    zinv2, det2 = zlib.multilook_zinv_det(s, win, wt, MODES[mode])
+    torch.cuda.synchronize()
+    assert torch.equal(zinv, zinv2) and torch.equal(det, det2)
+    check(zinv, det, reference(orc, s_np, win, wts), mode)
+    stn = st.cpu().numpy()
+    assert int(cnt[0]) == int((stn & 1).sum()) and int(cnt[1]) == int(((stn & 2) > 0).sum())
