@@ -1,12 +1,19 @@
 """GPU parity of the Wishart change statistic (wishart_stat_fwd / _bwd and the
 WishartStat autograd Function) against the FP64 oracle, through the C ABI.
 
-The GPU forms Z_t in FP32 (49 weighted products per entry for 7 x 7), then
-takes log-dets by the compensated route.  Per pixel, |q_gpu - q_oracle| is
-bounded by the FP32 rounding of Z (componentwise <= g u sqrt(Z_ii Z_jj)), which
-moves ln det by <= 3 g u cond(C) with C the unit-diagonal (correlation) form of
-Z, plus the logf roundings; the tests use Q_TOL per pixel and relative bounds
-for the sums that follow from it.
+Per-pixel bound on q (first order).  The GPU forms Z_t in FP32: each entry is
+an FMA chain of K = win^2 weighted products, so |dZ_ij| <= gamma_(K+1)
+sum_k w_k |S_i S_j| <= gamma_(K+1) sqrt(Z_ii Z_jj) (Cauchy-Schwarz, w_k >= 0),
+and Z1 + Z2 adds one rounding.  A perturbation dZ moves ln det Z by
+tr(Z^-1 dZ), at most sum_ij |(Z^-1)_ij| |dZ_ij| = g * S(Z) with
+    S(Z) = sum_ij |(Z^-1)_ij| sqrt(Z_ii Z_jj)
+(the absolute entry sum of the inverse of Z's correlation form).  The
+compensated log-dets add 4u each, logf one ulp of its result, and forming q
+rounds it a few times.  So, with u = 2^-24 and l = ln det,
+    |dq| <= gamma_(K+2) (S(Z1) + S(Z2) + 2 S(Z1 + Z2))
+            + 16u + 4u (|l1| + |l2| + 2 |l12| + 6 ln 2),
+computed per pixel from the oracle's FP64 window covariances; the tests allow
+1.25 times that.  The loss must be within the sum of the per-pixel bounds.
 """
 import numpy as np
 import pytest
@@ -16,8 +23,29 @@ from paper_1807_08084_gb300 import synth as S
 
 pytestmark = pytest.mark.gpu
 
-Q_ABS = 2e-4     # per-pixel q, absolute (|q| is O(1..10) on changed pixels)
 G_REL = 1e-4     # weight gradient, relative to its largest component
+U = 2.0 ** -24
+
+
+def gamma(k):
+    return k * U / (1 - k * U)
+
+
+def q_bound(orc, s1, s2, win, wts):
+    """[H*W] first-order bound on |q_gpu - q_oracle| (module docstring)."""
+    K = win * win
+    z1 = orc.multilook(s1, win, wts)
+    z2 = orc.multilook(s2, win, wts)
+    total = 16 * U + 4 * U * 6 * np.log(2)
+    for z, mult in ((z1, 1.0), (z2, 1.0), (z1 + z2, 2.0)):
+        inv, det = orc.zinv_det(z)
+        d = np.sqrt(z[[0, 5, 8]])  # sqrt of the diagonal
+        # sum_ij |W_ij| sqrt(Z_ii Z_jj): diagonal terms once, off-diagonal twice
+        S = inv[0] * d[0] ** 2 + inv[5] * d[1] ** 2 + inv[8] * d[2] ** 2
+        S = S + 2 * (np.hypot(inv[1], inv[2]) * d[0] * d[1] + np.hypot(inv[3], inv[4]) * d[0] * d[2]
+                     + np.hypot(inv[6], inv[7]) * d[1] * d[2])
+        total = total + mult * (gamma(K + 2) * S + 4 * U * np.abs(np.log(det)))
+    return 1.25 * total
 
 
 def pair(H, W, seed_shift=0):
@@ -44,8 +72,9 @@ def test_forward_and_backward_small(zlib, orc, win, shape):
     ref_loss, ref_q = orc.wishart_fwd(s1_np, s2_np, win, wt, want_map=True)
     ref_g = orc.wishart_bwd(s1_np, s2_np, win, wt, 1.0)
     dq = np.abs(q.cpu().numpy().ravel() - ref_q)
-    assert dq.max() <= Q_ABS, f"max |dq| {dq.max():.3e}"
-    assert abs(float(loss) - ref_loss) <= Q_ABS * H * W
+    qb = q_bound(orc, s1_np, s2_np, win, wt)
+    assert np.all(dq <= qb), f"max |dq|/bound {(dq / qb).max():.3f}"
+    assert abs(float(loss) - ref_loss) <= qb.sum()
     np.testing.assert_allclose(float(loss), q.double().sum().item(), rtol=1e-12, atol=1e-9)
     gg = g.cpu().numpy().astype(np.float64)
     assert np.abs(gg - ref_g).max() <= G_REL * np.abs(ref_g).max(), (
@@ -147,9 +176,11 @@ def test_full_size_pair(zlib, orc):
         c2 = w.looks(idx, 1).reshape(3, cy1 - cy0, cx1 - cx0)
         np.testing.assert_array_equal(s1[:, cy0:cy1, cx0:cx1].cpu().numpy(), c1)
         _, rq = orc.wishart_fwd(c1, c2, 7, wt, want_map=True)
-        rq = rq.reshape(cy1 - cy0, cx1 - cx0)[y0 - cy0:y1 - cy0, x0 - cx0:x1 - cx0]
+        qb = q_bound(orc, c1, c2, 7, wt).reshape(cy1 - cy0, cx1 - cx0)
+        sl = (slice(y0 - cy0, y1 - cy0), slice(x0 - cx0, x1 - cx0))
+        rq = rq.reshape(cy1 - cy0, cx1 - cx0)[sl]
         gq = q[y0:y1, x0:x1].cpu().numpy()
-        assert np.abs(gq - rq).max() <= Q_ABS
+        assert np.all(np.abs(gq - rq) <= qb[sl])
 
 
 def test_full_size_gradient_and_loss_vs_oracle(zlib, tmp_path):
@@ -173,4 +204,5 @@ def test_full_size_gradient_and_loss_vs_oracle(zlib, tmp_path):
     gg = g.cpu().numpy().astype(np.float64)
     err = np.abs(gg - ref_g).max() / np.abs(ref_g).max()
     assert err <= G_REL, f"grad rel err {err:.3e}"
-    assert abs(float(loss) - ref_loss) <= Q_ABS * w.H * w.W, (float(loss), ref_loss)
+    # the loss within 2e-4 per pixel (the per-pixel bound is typically 1e-5..1e-4)
+    assert abs(float(loss) - ref_loss) <= 2e-4 * w.H * w.W, (float(loss), ref_loss)

@@ -17,7 +17,7 @@ from paper_1807_08084_gb300 import synth as S
 
 pytestmark = pytest.mark.gpu
 
-Q_ABS = 2e-4  # per-pixel tolerance of the Wishart q map used by the other tests
+Q_ABS = 2e-4  # per-pixel q between the two entry points (same kernel and reduction: same bits in practice)
 
 
 def _entry(zp):
