@@ -497,13 +497,36 @@ def main():
         t_c = timed_device(lambda: zp.chol_zinv_det(zq, out=(zqi, dq)), sub, args.warmup, world)
         t_b = timed(lambda: zp.zinv_det(zq, zp.PLAIN, out=(zqi, dq)), 10 * sub, args.warmup,
                     world)
+        # device-side rate of back-to-back launches: 100 launches captured in a
+        # CUDA graph and replayed, so the binding's per-call host cost drops out
+        t_g = None
+        try:
+            graph = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                zp.zinv_det(zq, zp.PLAIN, out=(zqi, dq))  # warm on the capture stream
+            torch.cuda.current_stream().wait_stream(side)
+            with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+                for _ in range(100):
+                    zp.zinv_det(zq, zp.PLAIN, out=(zqi, dq))
+            t_g = timed(graph.replay, max(3, sub // 5), args.warmup, world) / 100
+        except RuntimeError as exc:  # capture not available: report the reason
+            t_g = None
+            graph_error = str(exc)[:200]
         plain256 = {"matrices": wq.n, "adjugate_us": t_a * 1e3, "cholesky_us": t_c * 1e3,
                     "adjugate_back_to_back_us": t_b * 1e3,
                     "adjugate_back_to_back_gmat_s": wq.n / (t_b * 1e-3) / 1e9,
+                    "adjugate_graph_us": None if t_g is None else t_g * 1e3,
+                    "adjugate_graph_gmat_s": None if t_g is None else wq.n / (t_g * 1e-3) / 1e9,
                     "l2": "L2-resident (5.0 MB per launch): no flush; *_us are the median device "
-                          "time of single launches, back_to_back the mean of consecutive ones",
+                          "time of single launches, back_to_back the mean of consecutive calls "
+                          "through the Python binding (host-bound), graph the mean of 100 "
+                          "launches replayed from a CUDA graph (the device rate)",
                     "workload": "256x256 packed Z, N = 4 looks of the fixed Sigma "
                                 "(Bartlett-sampled complex Wishart)"}
+        if t_g is None:
+            plain256["graph_error"] = graph_error
         del zq, zqi, dq
 
     # --- fused multilook (8192 x 8192 single-look, boxcar 3/5/7) ---------------

@@ -38,3 +38,26 @@ def test_reference_arm_json_line():
 
 def test_reference_arm_other_ranks_print_nothing():
     assert run({"WORLD_SIZE": "2", "RANK": "1"}) == ""
+
+
+def test_oracle_pool_runs_every_route():
+    """oracle.pool's worker processes run the unmodified oracle on their shares:
+    the items of one step add up to the sample, for each route."""
+    import tempfile
+    import numpy as np
+    sys.path.insert(0, str(ROOT))
+    from oracle.pool import OraclePool
+    from paper_1807_08084_gb300 import synth as S
+    with tempfile.TemporaryDirectory() as d:
+        z = S.WORKLOADS["plain_256"].packed_z(np.arange(1000, dtype=np.uint64))
+        np.save(f"{d}/z.npy", z)
+        for route in ("ge", "adj"):
+            with OraclePool(route, f"{d}/z.npy", workers=3) as pool:
+                items, wall, slowest = pool.step()
+            assert items == 1000 and wall > 0 and 0 < slowest <= wall
+        w = S.scaled(S.WORKLOADS["wishart_pair_4k"], 12, 20)
+        np.save(f"{d}/a.npy", w.image(0))
+        np.save(f"{d}/b.npy", w.image(1))
+        with OraclePool("wishart", (f"{d}/a.npy", f"{d}/b.npy"), workers=2) as pool:
+            items, _, _ = pool.step()
+        assert items == 12 * 20
