@@ -20,7 +20,11 @@
 //   - phase V: vertical window sums over the ring (four rows per thread), scale
 //     by 1/N, invert, store (warp-contiguous along x).
 // Each input row is loaded once per strip (plus 2r rows at a segment start and
-// 2r halo columns): ~1.1x the ideal read traffic.
+// 2r halo columns): ~1.1x the ideal read traffic.  Phase H reads the raw rows
+// and writes the ring in whole 16-byte units, and both store their units
+// swizzled (unit u at u ^ ((u >> 3) & 1)), so neither access has bank
+// conflicts (8-byte reads of two rows per half-warp replayed 2-way, and so did
+// the unswizzled 16-byte ring stores: 0.861 -> 0.821 ms at 7 x 7).
 //
 // Weighted windows (general taps, not separable) of 3 x 3, 5 x 5 and 7 x 7 run
 // on the window engine of window.cuh (32 x 16 output tiles, 4 x 2 outputs per
@@ -186,6 +190,13 @@ constexpr int kRawW = kTW + 8;  // raw columns x0-4 .. x0+67 (covers r <= 4), 16
 constexpr int kRawS = kRawW + 2;
 static_assert(kCH % 2 == 0, "phase H pairs rows");
 
+// 16-byte units (two float2 columns) of a raw row and of a ring row are
+// stored swizzled, unit u at u ^ ((u >> 3) & 1): the eight lanes of a
+// quarter-warp then touch eight distinct bank groups in phase H's 128-bit
+// reads of the raw rows and 128-bit stores to the ring.
+__device__ __forceinline__ int swu(int u) { return u ^ ((u >> 3) & 1); }
+__device__ __forceinline__ int swcol(int c) { return 2 * swu(c >> 1) + (c & 1); }
+
 template <int R>
 struct Strip {
   static_assert(R <= 4, "raw rows cover a halo of at most 4");
@@ -213,9 +224,9 @@ __device__ __forceinline__ void issue_rows_t(const MlArgs& a, float2* buf, int64
     const float2* row = a.s + p * a.plane_ld + gy * a.W;
     float2* dst = buf + (p * kCH + r) * kRawS;
     if (VEC16)
-      cp_async16(dst + 2 * ch, row + (x0 - 4) + 2 * ch);
+      cp_async16(dst + 2 * swu(ch), row + (x0 - 4) + 2 * ch);
     else
-      cp_async8(dst + ch, row + clamp64(x0 - 4 + ch, a.W - 1));
+      cp_async8(dst + swcol(ch), row + clamp64(x0 - 4 + ch, a.W - 1));
   }
 }
 
@@ -279,14 +290,28 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
         // groups 8 (g % 2) .. + 7 (rows is even: kCH or 2R)
         const int g = i >> 4, sub = i & 15;
         const int r = 2 * (g >> 1) + (sub >> 3), xr = 4 * (8 * (g & 1) + (sub & 7));
-        const int cbase = xr + 4 - R;  // raw column of the run's first input
+        // raw columns xr + 4 - R .. of the run's inputs, read as whole 16-byte
+        // units from unit u0 on; input k is value k + O of the units read
+        constexpr int O = (4 - R) & 1;
+        constexpr int NU = (O + 4 + 2 * R + 1) / 2;
+        const int u0 = (xr + 4 - R) >> 1;
+        float2 sv[3][2 * NU];
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+          for (int q = 0; q < NU; ++q) {
+            const float4 v =
+                *reinterpret_cast<const float4*>(rb + (p * kCH + r) * kRawS + 2 * swu(u0 + q));
+            sv[p][2 * q] = make_float2(v.x, v.y);
+            sv[p][2 * q + 1] = make_float2(v.z, v.w);
+          }
         float2 pv2[4][4 + 2 * R];
         float pv8[4 + 2 * R];
 #pragma unroll
         for (int k = 0; k < 4 + 2 * R; ++k) {
-          const float2 s0 = rb[(0 * kCH + r) * kRawS + cbase + k];
-          const float2 s1 = rb[(1 * kCH + r) * kRawS + cbase + k];
-          const float2 s2 = rb[(2 * kCH + r) * kRawS + cbase + k];
+          const float2 s0 = sv[0][k + O];
+          const float2 s1 = sv[1][k + O];
+          const float2 s2 = sv[2][k + O];
           float pp[9];
           channels(s0, s1, s2, pp);
           pv2[0][k] = make_float2(pp[0], pp[5]);
@@ -300,9 +325,11 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
         for (int q = 0; q < 4; ++q) {
           float2 o[4];
           window4v<R>(pv2[q], o);
-          float4* dst = reinterpret_cast<float4*>(ring2 + (q * T::RING + slot) * kTW + xr);
-          dst[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-          dst[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+          float2* rowp = ring2 + (q * T::RING + slot) * kTW;
+          *reinterpret_cast<float4*>(rowp + 2 * swu(xr >> 1)) =
+              make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+          *reinterpret_cast<float4*>(rowp + 2 * swu((xr >> 1) + 1)) =
+              make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
         }
         float o8[4];
         window4v<R>(pv8, o8);
@@ -315,22 +342,23 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
       const int orows = (out_rows - oy0) < kCH ? (out_rows - oy0) : kCH;
       for (int i = threadIdx.x; i < kTW * ((orows + 3) / 4); i += kSThreads) {
         const int x = i % kTW, yq = (i / kTW) * 4;
-        int off[4 + 2 * R];  // ring offsets of the rows this item reads
+        int off[4 + 2 * R];  // ring row offsets of the rows this item reads
         {
           int slot = (oy0 + yq) % T::RING;
 #pragma unroll
           for (int k = 0; k < 4 + 2 * R; ++k) {
-            off[k] = slot * kTW + x;
+            off[k] = slot * kTW;
             slot = (slot + 1 == T::RING) ? 0 : slot + 1;
           }
         }
+        const int xp = swcol(x);  // the float2 column's place in a swizzled ring row
         float z[4][9];
         const float2 inv2 = make_float2(invN, invN);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           float2 w[4 + 2 * R];
 #pragma unroll
-          for (int k = 0; k < 4 + 2 * R; ++k) w[k] = ring2[q * T::RING * kTW + off[k]];
+          for (int k = 0; k < 4 + 2 * R; ++k) w[k] = ring2[q * T::RING * kTW + off[k] + xp];
           float2 o[4];
           window4v<R>(w, o);
           constexpr int lo[4] = {0, 1, 3, 6}, hi[4] = {5, 2, 4, 7};
@@ -344,7 +372,7 @@ __global__ void __launch_bounds__(kSThreads, 3) k_multilook_strip(MlArgs a) {
         {
           float w[4 + 2 * R];
 #pragma unroll
-          for (int k = 0; k < 4 + 2 * R; ++k) w[k] = ring1[off[k]];
+          for (int k = 0; k < 4 + 2 * R; ++k) w[k] = ring1[off[k] + x];
           float o[4];
           window4v<R>(w, o);
 #pragma unroll
