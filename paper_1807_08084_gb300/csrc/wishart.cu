@@ -259,14 +259,19 @@ __device__ __forceinline__ void store_m(const WsArgs& a, float* G, int64_t ty0, 
 }
 
 // The three compensated inverses of every output of the tile, over the Z
-// slots of G (output o = tid + kWT j, so a warp reads one row's 32 entries of
-// a plane).  PAIRED: two outputs per pass (o and o + kWT) as packed pairs,
-// for the 3 x 3 and 5 x 5 windows; the 7 x 7 kernel, at its register limit
-// with the 49 tap accumulators live, ran 3% slower that way and takes one.
-template <bool PAIRED>
+// slots of G, two outputs per pass (o and o + kWT, so a warp reads one row's
+// 32 entries of a plane) as packed pairs.  The 3 x 3 and 5 x 5 kernels inline
+// the three inverses.  The 7 x 7 kernel (LOOPED) runs one inverse routine three
+// times, W12 = (Z1 + Z2)^-1 first, then W1 and W2, each turned into its M_t and
+// stored at once: with three inlined copies its larger body stalled on
+// instruction fetch, and the loop took 7% off its time (the 3 x 3 kernel lost
+// 5% that way).  Both forms round identically.
+template <bool LOOPED>
 __device__ __forceinline__ void bwd_inverses(const WsArgs& a, float* G, int64_t ty0,
                                              int64_t tx0) {
-  if constexpr (PAIRED) {
+  constexpr int TILE = kTH * kTW;
+  static_assert(TILE % (2 * kWT) == 0, "outputs o and o + kWT are in the tile");
+  if constexpr (!LOOPED) {
 #pragma unroll 1
     for (int o = threadIdx.x; o < kTH * kTW; o += 2 * kWT) {
       float2 z1[9], z2[9], z12[9], w1[9], w2[9], w12[9], d;
@@ -289,18 +294,40 @@ __device__ __forceinline__ void bwd_inverses(const WsArgs& a, float* G, int64_t 
     }
   } else {
 #pragma unroll 1
-    for (int o = threadIdx.x; o < kTH * kTW; o += kWT) {
-      float z1[9], z2[9], z12[9], w1[9], w2[9], w12[9], d;
+    for (int o = threadIdx.x; o < TILE; o += 2 * kWT) {
+      float2 z[9], w[9], w12[9], d;
+#pragma unroll 1
+      for (int m = 0; m < 3; ++m) {
+        // m = 0: Z1 + Z2; m = 1: Z1 (+ 0); m = 2: Z2 (0 +)
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        z1[c] = G[c * kTH * kTW + o];
-        z2[c] = G[(9 + c) * kTH * kTW + o];
-        z12[c] = z1[c] + z2[c];
+        for (int c = 0; c < 9; ++c) {
+          const float2 zero = make_float2(0.0f, 0.0f);
+          const float2 z1 = m != 2 ? make_float2(G[c * TILE + o], G[c * TILE + o + kWT]) : zero;
+          const float2 z2 =
+              m != 1 ? make_float2(G[(9 + c) * TILE + o], G[(9 + c) * TILE + o + kWT]) : zero;
+          z[c] = add_rn(z1, z2);
+        }
+        adjugate_inv_det_comp<float2>(z, w, d);
+        if (m == 0) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) w12[c] = w[c];
+          continue;
+        }
+        // M_t = W_t - 2 W12 over date t's Z slot, as store_m does
+        float* Gt = G + (m - 1) * 9 * TILE;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int oh = o + h * kWT;
+          const int64_t gy = ty0 + oh / kTW, gx = tx0 + oh % kTW;
+          const bool inside = gy < a.H && gx < a.W;
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            const float two = (c == 0 || c == 5 || c == 8) ? 1.0f : 2.0f;
+            const float wt = h ? w[c].y : w[c].x, wd = h ? w12[c].y : w12[c].x;
+            Gt[c * TILE + oh] = inside ? two * fmaf(-2.0f, wd, wt) : 0.0f;
+          }
+        }
       }
-      adjugate_inv_det_comp<float>(z1, w1, d);
-      adjugate_inv_det_comp<float>(z2, w2, d);
-      adjugate_inv_det_comp<float>(z12, w12, d);
-      store_m(a, G, ty0, tx0, o, w1, w2, w12);
     }
   }
 }
@@ -347,7 +374,7 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
         // per output: three compensated inverses, M_t = W_t - 2 W_12 in packed
         // gradient form over the Z slots
         __syncthreads();
-        bwd_inverses<(R < 3)>(a, G, ty0, tx0);
+        bwd_inverses<(R == 3)>(a, G, ty0, tx0);
         __syncthreads();
       }
       if (phase > 0) {
