@@ -47,6 +47,18 @@
  *                          Pinned by constant images, h -> infinity (box mean),
  *                          h -> 0 (identity), d >= 0 with d(i, i) = 0 and
  *                          symmetry, and brute-force numpy.
+ *   oracle_stochastic_distance, oracle_nlm_stochastic
+ *                          Bhattacharyya, Hellinger and Kullback-Leibler distances
+ *                          between equal-looks complex Wishart laws (§1's list of
+ *                          divergences), in closed form from the Wishart density,
+ *                          and the nonlocal-means filter weighted by exp(-d / h).
+ *                          Pinned by a Monte Carlo estimate of the defining
+ *                          integrals from sampled Wishart matrices, the
+ *                          identity S_i^-1 + S_j^-1 = S_i^-1 (S_i + S_j) S_j^-1
+ *                          (Bhattacharyya = L x the log-det distance above),
+ *                          closed forms for S_j = c S_i and diagonal pairs,
+ *                          invariance under a common congruence, symmetry,
+ *                          d(i, i) = 0, and brute-force numpy filters.
  *   oracle_wishart_fwd/bwd change statistic q = ln det Z1 + ln det Z2
  *                          - 2 ln det((Z1+Z2)/2) (the log of the likelihood-ratio
  *                          test the paper cites in §1, divided by the number of
@@ -731,6 +743,107 @@ void oracle_nlm_wishart(const double* z, int64_t H, int64_t W, int radius, doubl
             for (int k = 0; k < 9; ++k) out[k * n + i] = acc[k] / wsum;
         }
     free(ld);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stochastic distances between the complex Wishart laws W(S_i, L) and      */
+/* W(S_j, L) of two pixels with the same number of looks L and m = 3 (§1     */
+/* lists Kullback-Leibler, Hellinger, Renyi, Bhattacharyya, triangular and   */
+/* harmonic divergences among the uses of det Z and Z^-1).  From the density */
+/*     f(Z) = c(L) |Z|^(L-m) |S|^-L exp(-L tr(S^-1 Z)),  E[Z] = S:           */
+/*   Bhattacharyya  d_B = -ln of the integral of sqrt(f_i f_j)               */
+/*                      = L [ln det((S_i^-1 + S_j^-1)/2)                     */
+/*                           + (ln det S_i + ln det S_j)/2],                 */
+/*   Hellinger      d_H = 1 - that integral = 1 - exp(-d_B),                 */
+/*   Kullback-Leibler (the mean of the two directed divergences)             */
+/*                  d_KL = L [(tr(S_i^-1 S_j) + tr(S_j^-1 S_i))/2 - m].      */
+/* All three are >= 0, symmetric, and 0 iff S_i = S_j.  The oracle takes     */
+/* them as written, with Gauss-Jordan inverses and elimination dets.         */
+/* ------------------------------------------------------------------------ */
+
+#define ORACLE_DIST_BHATTACHARYYA 0
+#define ORACLE_DIST_HELLINGER 1
+#define ORACLE_DIST_KULLBACK_LEIBLER 2
+
+/* tr(X Y) = sum_r sum_c X[r][c] Y[c][r] (real for Hermitian X, Y). */
+static double trace_of_product(const mat3* X, const mat3* Y)
+{
+    cplx t = 0;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+#if ORACLE_MUTANT == 13
+            t += X->m[r][c] * Y->m[r][c]; /* mutant: Y's element not transposed */
+#else
+            t += X->m[r][c] * Y->m[c][r];
+#endif
+    return creal(t);
+}
+
+/* One pixel pair, given both covariances, their inverses and log-dets. */
+static double stochastic_distance(const mat3* Si, const mat3* Sj, const mat3* Ii,
+                                  const mat3* Ij, double ldi, double ldj, double looks,
+                                  int dist)
+{
+    if (dist == ORACLE_DIST_KULLBACK_LEIBLER)
+        return looks * (0.5 * (trace_of_product(Ii, Sj) + trace_of_product(Ij, Si)) - 3.0);
+    mat3 M;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M.m[r][c] = 0.5 * (Ii->m[r][c] + Ij->m[r][c]);
+    double dB = looks * (logdet(&M) + 0.5 * (ldi + ldj));
+    if (dist == ORACLE_DIST_HELLINGER)
+#if ORACLE_MUTANT == 14
+        return 1.0 - exp(-0.5 * dB); /* mutant: square root of the coefficient */
+#else
+        return 1.0 - exp(-dB);
+#endif
+    return dB;
+}
+
+/* d(S_i, S_j) for packed zi, zj (nine doubles each); NaN for an unknown dist
+ * or a singular matrix. */
+double oracle_stochastic_distance(const double* zi, const double* zj, double looks, int dist)
+{
+    if (dist < 0 || dist > 2) return NAN;
+    mat3 Si = unpack(zi, 1, 0), Sj = unpack(zj, 1, 0), Ii, Ij;
+    if (ge_inverse(&Si, &Ii) || ge_inverse(&Sj, &Ij)) return NAN;
+    return stochastic_distance(&Si, &Sj, &Ii, &Ij, logdet(&Si), logdet(&Sj), looks, dist);
+}
+
+/* Nonlocal means with weights w_ij = exp(-d(i, j) / h) over the in-image
+ * neighbours within the search radius (d including the factor L); the
+ * Bhattacharyya case equals oracle_nlm_wishart. */
+void oracle_nlm_stochastic(const double* z, int64_t H, int64_t W, int radius, double looks,
+                           double h, int dist, double* out)
+{
+    int64_t n = H * W;
+    mat3* inv = (mat3*)malloc((size_t)n * sizeof(mat3));
+    double* ld = (double*)malloc((size_t)n * sizeof(double));
+    for (int64_t p = 0; p < n; ++p) {
+        mat3 A = unpack(z, n, p);
+        ld[p] = logdet(&A);
+        if (ge_inverse(&A, &inv[p])) ld[p] = NAN;
+    }
+    for (int64_t y = 0; y < H; ++y)
+        for (int64_t x = 0; x < W; ++x) {
+            int64_t i = y * W + x;
+            mat3 Si = unpack(z, n, i);
+            double acc[9] = {0}, wsum = 0.0;
+            for (int dy = -radius; dy <= radius; ++dy)
+                for (int dx = -radius; dx <= radius; ++dx) {
+                    int64_t yy = y + dy, xx = x + dx;
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    int64_t j = yy * W + xx;
+                    mat3 Sj = unpack(z, n, j);
+                    double d = stochastic_distance(&Si, &Sj, &inv[i], &inv[j], ld[i], ld[j],
+                                                   looks, dist);
+                    double w = exp(-d / h);
+                    for (int k = 0; k < 9; ++k) acc[k] += w * z[k * n + j];
+                    wsum += w;
+                }
+            for (int k = 0; k < 9; ++k) out[k * n + i] = acc[k] / wsum;
+        }
+    free(ld);
+    free(inv);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -15,7 +15,10 @@ not agree with what the paper and the mathematics fix:
 * brute-force Python loops for the window covariance (Eq. ZN);
 * central finite differences through numpy.linalg for the gradients;
 * q <= 0, q(Z, Z) = 0, Euler homogeneity and date-swap symmetry for the Wishart
-  change statistic.
+  change statistic;
+* Monte Carlo estimates, from sampled complex Wishart matrices, of the integrals
+  that define the Bhattacharyya and Kullback-Leibler distances, and the
+  closed forms and invariances of those distances.
 
 ``test_mutants_are_caught`` builds the oracle with each planted mistake and
 requires that at least one check fails for each.
@@ -371,10 +374,116 @@ def check_nlm(o):
     np.testing.assert_allclose(o.nlm_wishart(z, H, W, rad, L, 1e-9), z, rtol=1e-12)
 
 
+def _wishart_samples(rng, S, L, n):
+    """n draws of Z = (1/L) sum_l s_l s_l^H, s_l ~ CN(0, S): the complex
+    Wishart law W(S, L) of an L-look covariance (E[Z] = S)."""
+    C = np.linalg.cholesky(S)
+    g = (rng.standard_normal((n, L, 3)) + 1j * rng.standard_normal((n, L, 3))) / np.sqrt(2)
+    s = g @ C.T                                   # rows s_l = C g_l
+    return np.einsum("nli,nlj->nij", s, s.conj()) / L
+
+
+def check_stochastic_distances(o):
+    """Stochastic distances between equal-looks Wishart laws (§1's list), pinned
+    to the density they are defined from and to the mathematics, not to their
+    closed forms alone."""
+    from paper_1807_08084_gb300 import synth as S
+    B, HL, KL = o.BHATTACHARYYA, o.HELLINGER, o.KULLBACK_LEIBLER
+    rng = np.random.default_rng(23)
+    L = 4.0
+    Z = pack(random_pd(rng, 40, cond_max=1e2))
+    A = unpack(Z)
+    for k in range(0, 40, 2):
+        zi, zj = Z[:, k], Z[:, k + 1]
+        dB, dH, dK = (o.stochastic_distance(zi, zj, L, d) for d in (B, HL, KL))
+        # Bhattacharyya through the inverses equals the log-det of the mean:
+        # S_i^-1 + S_j^-1 = S_i^-1 (S_i + S_j) S_j^-1
+        assert abs(dB - L * o.pair_distance(zi, zj)) < 1e-12 * max(1.0, dB)
+        assert abs(dH - (1 - np.exp(-dB))) < 1e-14
+        # symmetric, >= 0, zero on the diagonal
+        for d, v in ((B, dB), (HL, dH), (KL, dK)):
+            assert v > 0 and abs(o.stochastic_distance(zj, zi, L, d) - v) < 1e-12 * max(1.0, v)
+            assert abs(o.stochastic_distance(zi, zi, L, d)) < 1e-12
+        # invariant under a common congruence S -> T S T^H (T invertible, complex)
+        T = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        ti, tj = pack(T @ A[k] @ T.conj().T), pack(T @ A[k + 1] @ T.conj().T)
+        for d, v in ((B, dB), (HL, dH), (KL, dK)):
+            assert abs(o.stochastic_distance(ti, tj, L, d) - v) < 1e-8 * max(1.0, v)
+        # KL against numpy: traces of S_i^-1 S_j
+        ref = L * (0.5 * (np.trace(np.linalg.solve(A[k], A[k + 1]))
+                          + np.trace(np.linalg.solve(A[k + 1], A[k]))).real - 3)
+        assert abs(dK - ref) < 1e-10 * max(1.0, ref)
+    # closed forms: S_j = c S_i, and diagonal pairs (per-component sums)
+    for c in (0.25, 0.9, 3.0):
+        zi = Z[:, 0]
+        dB = 3 * L * np.log((np.sqrt(c) + 1 / np.sqrt(c)) / 2)
+        assert abs(o.stochastic_distance(zi, c * zi, L, B) - dB) < 1e-12
+        assert abs(o.stochastic_distance(zi, c * zi, L, HL) - (1 - np.exp(-dB))) < 1e-12
+        assert abs(o.stochastic_distance(zi, c * zi, L, KL) - 3 * L * ((c + 1 / c) / 2 - 1)) < 1e-12
+    a, b = np.array([1.0, 0.3, 7.0]), np.array([2.0, 0.3, 0.5])
+    za, zb = np.zeros(9), np.zeros(9)
+    za[[0, 5, 8]], zb[[0, 5, 8]] = a, b
+    assert abs(o.stochastic_distance(za, zb, L, KL) - L * ((a / b + b / a) / 2 - 1).sum()) < 1e-12
+    assert abs(o.stochastic_distance(za, zb, L, B)
+               - L * np.log((np.sqrt(a / b) + np.sqrt(b / a)) / 2).sum()) < 1e-12
+    # Monte Carlo from the Wishart density: with Z ~ W(S_i, L),
+    #   f_j / f_i (Z) = (det S_i / det S_j)^L exp(-L tr((S_j^-1 - S_i^-1) Z)),
+    # E_i[sqrt(f_j / f_i)] = exp(-d_B) and E_i[ln(f_i / f_j)] = D(i || j).
+    Li = 4
+    Si = A[2]
+    Sj = Si + 0.15 * np.diag(np.diag(Si).real) + 0.05 * A[3]
+    zi, zj = pack(Si[None])[:, 0], pack(Sj[None])[:, 0]
+    n = 200_000
+    lr = {}
+    for (P, Q), key in (((Si, Sj), "ij"), ((Sj, Si), "ji")):
+        Zs = _wishart_samples(rng, P, Li, n)
+        D = np.linalg.inv(Q) - np.linalg.inv(P)
+        tr = np.einsum("ab,nba->n", D, Zs).real
+        lr[key] = Li * (np.log(np.linalg.det(P).real / np.linalg.det(Q).real) - tr)  # ln f_Q/f_P
+    bc = np.exp(0.5 * lr["ij"])
+    d_mc = -np.log(bc.mean())
+    se = bc.std() / np.sqrt(n) / bc.mean()
+    assert abs(o.stochastic_distance(zi, zj, Li, B) - d_mc) < 5 * se + 1e-3 * d_mc
+    kl = 0.5 * (np.mean(-lr["ij"]) + np.mean(-lr["ji"]))
+    se_kl = 0.5 * (lr["ij"].std() + lr["ji"].std()) / np.sqrt(n)
+    assert abs(o.stochastic_distance(zi, zj, Li, KL) - kl) < 5 * se_kl
+    # the filters: Bhattacharyya weights are the log-det filter's; Hellinger
+    # and Kullback-Leibler against a numpy brute force on a tiny image
+    H, W, rad, h = 6, 7, 2, 0.8
+    z = S.scaled(S.WORKLOADS["paper_meas_shaped"], H, W).packed_z().astype(np.float64)
+    np.testing.assert_allclose(o.nlm_stochastic(z, H, W, rad, L, h, B),
+                               o.nlm_wishart(z, H, W, rad, L, h), rtol=1e-11,
+                               atol=1e-13 * np.abs(z).max())
+    Az = unpack(z)
+    inv = np.linalg.inv(Az)
+    ld = np.linalg.slogdet(Az)[1]
+    for dist in (HL, KL):
+        out = o.nlm_stochastic(z, H, W, rad, L, h, dist)
+        ref = np.empty_like(out)
+        for y in range(H):
+            for x in range(W):
+                i = y * W + x
+                acc, ws = np.zeros(9), 0.0
+                for yy in range(max(0, y - rad), min(H, y + rad + 1)):
+                    for xx in range(max(0, x - rad), min(W, x + rad + 1)):
+                        j = yy * W + xx
+                        if dist == KL:
+                            d = L * (0.5 * np.trace(inv[i] @ Az[j] + inv[j] @ Az[i]).real - 3)
+                        else:
+                            d = 1 - np.exp(-L * (np.linalg.slogdet((inv[i] + inv[j]) / 2)[1]
+                                                 + 0.5 * (ld[i] + ld[j])))
+                        wgt = np.exp(-d / h)
+                        acc += wgt * z[:, j]
+                        ws += wgt
+                ref[:, i] = acc / ws
+        np.testing.assert_allclose(out, ref, rtol=1e-11, atol=1e-13 * np.abs(z).max())
+
+
 CHECKS = [check_sigma_exact, check_random_vs_numpy, check_identity_and_hermitian,
           check_det_properties, check_closed_forms, check_ill_conditioned_det,
           check_multilook_brute,
-          check_bwd_finite_differences, check_wishart, check_nlm, check_blockdiag]
+          check_bwd_finite_differences, check_wishart, check_nlm, check_blockdiag,
+          check_stochastic_distances]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=lambda c: c.__name__)
@@ -396,6 +505,8 @@ MUTANTS = {
     10: "gradient sign of the W G W term",
     11: "elimination det ignores the permutation sign",
     12: "nonlocal means drops the 1/2 of the pair mean",
+    13: "trace of a product takes the second factor untransposed",
+    14: "Hellinger distance from the square root of the Bhattacharyya coefficient",
 }
 
 
