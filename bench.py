@@ -630,6 +630,21 @@ def main():
         nlm["speedup_adjugate_vs_cholesky"] = nlm["cholesky"]["ms"] / nlm["adjugate"]["ms"]
         nlm["workload"] = (f"{wn.H}x{wn.W} packed Z (scale_16k generator), radius 11 "
                            "(23 x 23 window), L = 16, h = 1")
+        # the other stochastic distances (nlm_stochastic): Hellinger shares the
+        # per-pair determinant; Kullback-Leibler takes two traces with the
+        # per-pixel inverses instead
+        hel = {}
+        for name, meth in (("adjugate", zp.NLM_ADJUGATE), ("cholesky", zp.NLM_CHOLESKY)):
+            t = timed(lambda: zp.nlm_stochastic(zn, 11, 16.0, 0.25, zp.NLM_HELLINGER, meth,
+                                                out=zo), max(3, sub // 5), args.warmup, world)
+            hel[name] = {"ms": t, "gpairs_s": pairs / (t * 1e-3) / 1e9}
+        hel["speedup_adjugate_vs_cholesky"] = hel["cholesky"]["ms"] / hel["adjugate"]["ms"]
+        hel["h"] = 0.25
+        nlm["hellinger"] = hel
+        t = timed(lambda: zp.nlm_stochastic(zn, 11, 16.0, 4.0, zp.NLM_KULLBACK_LEIBLER,
+                                            zp.NLM_ADJUGATE, out=zo), max(3, sub // 5),
+                  args.warmup, world)
+        nlm["kullback_leibler"] = {"ms": t, "gpairs_s": pairs / (t * 1e-3) / 1e9, "h": 4.0}
         del zn, zo
 
     # --- Wishart change statistic (two 4096 x 4096 dates, 7 x 7 window) -------

@@ -195,6 +195,36 @@ int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int radius, fl
                 float h, int method, float* z_out, void* stream);
 
 /*
+ * nlm_stochastic -- the nonlocal-means filter of nlm_wishart with a choice of
+ * stochastic distance between the pixels' complex Wishart laws of `looks`
+ * looks (§1 lists the Kullback-Leibler, Hellinger, Renyi, Bhattacharyya,
+ * triangular and harmonic divergences among the computations that need only
+ * det Z and Z^-1).  Weights w_ij = exp(-d(i, j) / h), Z'_i as nlm_wishart, with
+ * d (closed forms for equal looks, m = 3):
+ *   ZINV_NLM_BHATTACHARYYA    d = L [ln det((Z_i + Z_j)/2) - (ln det Z_i + ln det Z_j)/2]
+ *                             (equal to L [ln det((Z_i^-1 + Z_j^-1)/2) + (ln det Z_i
+ *                             + ln det Z_j)/2]); the filter of nlm_wishart.
+ *   ZINV_NLM_HELLINGER        d = 1 - exp(-d_Bhattacharyya)   (in [0, 1)).
+ *   ZINV_NLM_KULLBACK_LEIBLER d = L [(tr(Z_i^-1 Z_j) + tr(Z_j^-1 Z_i))/2 - 3], the mean
+ *                             of the two directed divergences; Z^-1 of every pixel
+ *                             by Algorithm 2 (compensated cofactors and det).
+ *   method    the per-pair determinant of Bhattacharyya and Hellinger:
+ *             ZINV_NLM_ADJUGATE (Algorithm 2) or ZINV_NLM_CHOLESKY (Algorithm 1).
+ *             Kullback-Leibler takes no per-pair determinant and accepts
+ *             ZINV_NLM_ADJUGATE only.
+ *   z, H, W, ld, radius, looks, h, z_out, stream  as nlm_wishart.
+ * Returns ZINV_ERR_ARG for an unknown distance or method, or a method the
+ * distance does not take, before any device work.
+ */
+#define ZINV_NLM_ADJUGATE 0
+#define ZINV_NLM_CHOLESKY 1
+#define ZINV_NLM_BHATTACHARYYA 0
+#define ZINV_NLM_HELLINGER 1
+#define ZINV_NLM_KULLBACK_LEIBLER 2
+int nlm_stochastic(const float* z, int64_t H, int64_t W, int64_t ld, int radius, float looks,
+                   float h, int distance, int method, float* z_out, void* stream);
+
+/*
  * Wishart change statistic between two dates with a learnable window (the
  * likelihood-ratio change test the paper lists among the consumers of det Z and
  * Z^-1, §1).  For every pixel p of two co-registered H x W single-look images

@@ -79,6 +79,9 @@ def _declare_extra(lib):
     lib.nlm_wishart.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_float,
                                 ctypes.c_float, ctypes.c_int, _P, _P]
     lib.nlm_wishart.restype = ctypes.c_int
+    lib.nlm_stochastic.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_int, ctypes.c_int, _P, _P]
+    lib.nlm_stochastic.restype = ctypes.c_int
     lib.wishart_workspace_bytes.argtypes = [_I64, _I64, ctypes.c_int]
     lib.wishart_workspace_bytes.restype = ctypes.c_size_t
     lib.wishart_stat_fwd.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
@@ -304,6 +307,34 @@ def nlm_wishart(z: torch.Tensor, radius: int = 11, looks: float = 16.0, h: float
         rc = lib.nlm_wishart(_ptr(z), H, W, ld, int(radius), float(looks), float(h), int(method),
                              _ptr(out), _stream(z.device))
     _check(rc, "nlm_wishart")
+    return out
+
+
+NLM_BHATTACHARYYA = 0
+NLM_HELLINGER = 1
+NLM_KULLBACK_LEIBLER = 2
+
+
+def nlm_stochastic(z: torch.Tensor, radius: int = 11, looks: float = 16.0, h: float = 1.0,
+                   distance: int = NLM_BHATTACHARYYA, method: int = NLM_ADJUGATE,
+                   out: torch.Tensor | None = None) -> torch.Tensor:
+    """Nonlocal-means filter of a packed [9, H, W] image with weights
+    exp(-d / h), d the Bhattacharyya, Hellinger or Kullback-Leibler distance
+    between the pixels' equal-looks Wishart laws; the per-pair determinant of
+    the first two by Algorithm 2 (NLM_ADJUGATE) or Algorithm 1 (NLM_CHOLESKY)."""
+    lib = load()
+    if z.dim() != 3:
+        raise ValueError("z must be [9, H, W]")
+    n, ld = _planes(z)
+    H, W = z.shape[1], z.shape[2]
+    if out is None:
+        out = torch.empty((9, H, W), dtype=torch.float32, device=z.device)
+    else:
+        _out(out, (9, H, W), z.device, "out")
+    with torch.cuda.device(z.device):
+        rc = lib.nlm_stochastic(_ptr(z), H, W, ld, int(radius), float(looks), float(h),
+                                int(distance), int(method), _ptr(out), _stream(z.device))
+    _check(rc, "nlm_stochastic")
     return out
 
 

@@ -1,29 +1,43 @@
-// nlm.cu -- nonlocal-means filter of a packed covariance image with the Wishart
-// equal-looks distance (the paper's motivating workload, §1: for every pixel,
-// a 23 x 23 search window of determinants of 3x3 Hermitian matrices).
+// nlm.cu -- nonlocal-means filter of a packed covariance image with stochastic
+// distances between the pixels' complex Wishart laws of L looks (the paper's
+// motivating workload, §1: for every pixel, a 23 x 23 search window of 3x3
+// Hermitian determinants or inverses; §1 lists these divergences among the
+// uses of det Z and Z^-1).
 //
-// For pixels i, j:  d(i, j) = ln det((Z_i + Z_j)/2) - (ln det Z_i + ln det Z_j)/2,
-// w_ij = exp(-L d(i, j) / h) over the in-image neighbours within the search
-// radius, and Z'_i = sum_j w_ij Z_j / sum_j w_ij.
+// For pixels i, j the weight is w_ij = exp(-d(i, j) / h) over the in-image
+// neighbours within the search radius, and Z'_i = sum_j w_ij Z_j / sum_j w_ij,
+// with d one of (closed forms for equal looks, m = 3):
+//   Bhattacharyya  d_B = L [ln det((Z_i + Z_j)/2) - (ln det Z_i + ln det Z_j)/2]
+//                  (= L [ln det((Z_i^-1 + Z_j^-1)/2) + (ln det Z_i + ln det Z_j)/2],
+//                  as Z_i^-1 + Z_j^-1 = Z_i^-1 (Z_i + Z_j) Z_j^-1),
+//   Hellinger      d_H = 1 - exp(-d_B),
+//   Kullback-Leibler (mean of both directions)
+//                  d_KL = L [(tr(Z_i^-1 Z_j) + tr(Z_j^-1 Z_i))/2 - 3].
 //
-// In base 2, with D_ij = det(Z_i + Z_j) and h_i = log2(det Z_i) / 2:
-//     w_ij = 2^(-p t_ij),  t_ij = max(log2 D_ij - (3 + h_i) - h_j, 0),  p = L / h,
-// (det((Z_i + Z_j)/2) = D_ij / 8 for 3x3 matrices; t >= 0 in exact arithmetic,
-// the clamp absorbs rounding).  h_i is formed once per staged pixel (compensated
-// route); per pair the work is D_ij -- 529 determinants per pixel for a 23 x 23
-// window -- one log2 and one exp2.  D_ij is computed either by Algorithm 2's
-// cofactor expansion (Eq. adjoint_elements, Eq. detr: no division, no square
-// root) or by Algorithm 1's Cholesky route (three square roots, two
-// reciprocals); everything else is shared, so the two can be compared where
-// arithmetic, not memory, sets the time.
+// Bhattacharyya and Hellinger, in base 2 with D_ij = det(Z_i + Z_j) and
+// h_i = log2(det Z_i) / 2:  d_B = L ln2 t_ij,  t_ij = max(log2 D_ij - (3 + h_i) - h_j, 0)
+// (det((Z_i + Z_j)/2) = D_ij / 8; t >= 0 in exact arithmetic, the clamp absorbs
+// rounding), so w = 2^(-(L/h) t) and, for Hellinger, w = 2^(-(log2 e / h)(1 - 2^(-L t))).
+// h_i is formed once per staged pixel (compensated route); per pair the work is
+// D_ij -- 529 determinants per pixel for a 23 x 23 window -- one log2 and one
+// or two exp2.  D_ij is computed either by Algorithm 2's cofactor expansion
+// (Eq. adjoint_elements, Eq. detr: no division, no square root) or by
+// Algorithm 1's Cholesky route (three square roots, two reciprocals);
+// everything else is shared, so the two can be compared where arithmetic, not
+// memory, sets the time.
+// Kullback-Leibler: Z^-1 of every staged pixel by Algorithm 2 with compensated
+// (Dot2) cofactors and det, once per staged pixel; per pair two traces of
+// packed Hermitian products (nine FMAs each: tr(A B) = a a' + d d' + f f' +
+// 2 (Re b Re b' + Im b Im b' + ...)) and one exp2.
 //
 // Tiles of 32 x 16 outputs, 256 threads; each thread owns two vertically
 // adjacent outputs A and B, held as the two halves of packed f32x2 values:
-// every neighbour Z_j loaded from shared memory serves both outputs' pairs
-// (one packed sum Z_A + Z_j | Z_B + Z_j, one packed determinant by Algorithm 2,
-// one packed weighted accumulation).  The rows of the two windows are walked
+// every neighbour loaded from shared memory serves both outputs' pairs (one
+// packed sum Z_A + Z_j | Z_B + Z_j, one packed determinant by Algorithm 2, one
+// packed weighted accumulation).  The rows of the two windows are walked
 // together; a row outside one output's window gets weight 0 for that output.
-// The tile plus a halo of the search radius (Z and h) sits in shared memory.
+// The tile plus a halo of the search radius (Z and h, or Z and Z^-1) sits in
+// shared memory.
 #include "common.cuh"
 #include "pixel.cuh"
 
@@ -34,13 +48,24 @@ constexpr int kNT = 256;
 constexpr int kNW = 32;  // tile width
 constexpr int kNH = 16;  // tile height: 8 row pairs
 
+// Distances (the values of nlm_stochastic's `distance`).
+constexpr int kBhattacharyya = 0, kHellinger = 1, kKullbackLeibler = 2;
+
 struct NlmArgs {
   const float* z;
   int64_t H, W, ld;
   int radius;
-  float p;  // L / h
+  float p;      // Bhattacharyya: L / h; Kullback-Leibler: L log2(e) / h
+  float looks;  // Hellinger: L
+  float qh;     // Hellinger: log2(e) / h
   float* out;
 };
+
+// Shared-memory planes per staged pixel: Z and h, or Z and Z^-1.
+template <int DIST>
+constexpr int nlm_planes() {
+  return DIST == kKullbackLeibler ? 18 : 10;
+}
 
 // det by Algorithm 1's factorization: (l00 l11 l22)^2 with l00 = sqrt(a), the
 // first column scaled by 1/l00, l11 = sqrt(d - |l10|^2), l21 scaled by 1/l11,
@@ -61,12 +86,13 @@ __device__ __forceinline__ float det_cholesky(const float x[9]) {
   return q * q;
 }
 
-template <int METHOD, int RAD>
+template <int METHOD, int RAD, int DIST>
 __global__ void __launch_bounds__(kNT, 2) k_nlm(NlmArgs a) {
   constexpr int SW = kNW + 2 * RAD, SH = kNH + 2 * RAD;
+  constexpr bool KL = DIST == kKullbackLeibler;
   extern __shared__ __align__(16) float smem[];
   float* Zs = smem;                // [9][SH][SW]
-  float* Hs = smem + 9 * SH * SW;  // [SH][SW] half log2-dets
+  float* Hs = smem + 9 * SH * SW;  // [SH][SW] half log2-dets, or [9][SH][SW] Z^-1 (KL)
   const int64_t n = a.H * a.W;
   const int64_t tiles_x = (a.W + kNW - 1) / kNW;
   const int64_t tiles = tiles_x * ((a.H + kNH - 1) / kNH);
@@ -86,14 +112,23 @@ __global__ void __launch_bounds__(kNT, 2) k_nlm(NlmArgs a) {
         v[c] = __ldg(a.z + c * a.ld + q);
         Zs[(c * SH + sy) * SW + sx] = v[c];
       }
-      const dd<float> dt = det_comp<float>(v);
-      Hs[sy * SW + sx] = 0.5f * (log2f(dt.hi) + (dt.lo / dt.hi) * inv_ln2);
+      if constexpr (KL) {
+        float w[9], dt;
+        adjugate_inv_det_comp<float>(v, w, dt);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Hs[(c * SH + sy) * SW + sx] = w[c];
+      } else {
+        const dd<float> dt = det_comp<float>(v);
+        Hs[sy * SW + sx] = 0.5f * (log2f(dt.hi) + (dt.lo / dt.hi) * inv_ln2);
+      }
     }
     __syncthreads();
     const int64_t gyA = y0 + ty, gx = x0 + tx;
     if (gyA >= a.H || gx >= a.W) continue;
     const bool hasB = gyA + 1 < a.H;
     const int cy = ty + RAD, cx = tx + RAD;  // shared-memory position of output A
+    // own values of A | B: Z, and for KL Z and Z^-1 with the off-diagonal
+    // packed reals doubled (the trace's factor 2, exact)
     float2 zi[9], acc[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
@@ -101,8 +136,20 @@ __global__ void __launch_bounds__(kNT, 2) k_nlm(NlmArgs a) {
       zi[c] = make_float2(za, hasB ? Zs[(c * SH + cy + 1) * SW + cx] : za);
       acc[c] = make_float2(0.0f, 0.0f);
     }
-    const float kA = 3.0f + Hs[cy * SW + cx];
-    const float kB = hasB ? 3.0f + Hs[(cy + 1) * SW + cx] : kA;
+    float2 ii2[KL ? 9 : 1], zi2[KL ? 9 : 1];
+    float kA = 0.0f, kB = 0.0f;
+    if constexpr (KL) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const float two = (c == 0 || c == 5 || c == 8) ? 1.0f : 2.0f;
+        const float ia = Hs[(c * SH + cy) * SW + cx];
+        ii2[c] = make_float2(two * ia, two * (hasB ? Hs[(c * SH + cy + 1) * SW + cx] : ia));
+        zi2[c] = make_float2(two * zi[c].x, two * zi[c].y);
+      }
+    } else {
+      kA = 3.0f + Hs[cy * SW + cx];
+      kB = hasB ? 3.0f + Hs[(cy + 1) * SW + cx] : kA;
+    }
     // in-image rows of the two windows (B's starts one row later) and columns
     const int64_t a_lo = gyA - RAD < 0 ? 0 : gyA - RAD;
     const int64_t a_hi = gyA + RAD >= a.H ? a.H - 1 : gyA + RAD;
@@ -110,7 +157,7 @@ __global__ void __launch_bounds__(kNT, 2) k_nlm(NlmArgs a) {
     const int64_t b_hi = hasB ? (gyA + 1 + RAD >= a.H ? a.H - 1 : gyA + 1 + RAD) : a_hi;
     const int dx0 = (int)(gx - RAD < 0 ? -gx : -RAD);
     const int dx1 = (int)(gx + RAD >= a.W ? a.W - 1 - gx : RAD);
-    const float np = -a.p;
+    const float np = -a.p, nl = -a.looks, nq = -a.qh;
     float2 ws = make_float2(0.0f, 0.0f);
     for (int64_t gy = a_lo; gy <= b_hi; ++gy) {
       const float2 m = make_float2(gy <= a_hi ? 1.0f : 0.0f, hasB && gy >= b_lo ? 1.0f : 0.0f);
@@ -119,26 +166,54 @@ __global__ void __launch_bounds__(kNT, 2) k_nlm(NlmArgs a) {
       const float* hrow = Hs + srow * SW + cx;
       for (int dx = dx0; dx <= dx1; ++dx) {
         float zj[9];
-        float2 zs[9];
+        float2 w;
+        if constexpr (KL) {
+          // t = (tr(Z_A^-1 Z_j) + tr(Z_j^-1 Z_A)) / 2 - 3, both traces in
+          // channel order as packed FMAs
+          float ij[9];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-          zj[c] = zrow[c * SH * SW + dx];
-          zs[c] = add_rn(zi[c], make_float2(zj[c], zj[c]));
-        }
-        float2 D;
-        if constexpr (METHOD == 0) {
-          D = det_adjugate<float2>(zs);
+          for (int c = 0; c < 9; ++c) {
+            zj[c] = zrow[c * SH * SW + dx];
+            ij[c] = hrow[c * SH * SW + dx];
+          }
+          float2 t1 = mul_rn(ii2[0], make_float2(zj[0], zj[0]));
+          float2 t2 = mul_rn(zi2[0], make_float2(ij[0], ij[0]));
+#pragma unroll
+          for (int c = 1; c < 9; ++c) {
+            t1 = fma_rn(ii2[c], make_float2(zj[c], zj[c]), t1);
+            t2 = fma_rn(zi2[c], make_float2(ij[c], ij[c]), t2);
+          }
+          const float2 tk = fma_rn(make_float2(0.5f, 0.5f), add_rn(t1, t2),
+                                   make_float2(-3.0f, -3.0f));
+          w = mul_rn(make_float2(exp2f(np * fmaxf(tk.x, 0.0f)), exp2f(np * fmaxf(tk.y, 0.0f))),
+                     m);
         } else {
-          float xa[9], xb[9];
+          float2 zs[9];
 #pragma unroll
-          for (int c = 0; c < 9; ++c) xa[c] = zs[c].x, xb[c] = zs[c].y;
-          D = make_float2(det_cholesky(xa), det_cholesky(xb));
+          for (int c = 0; c < 9; ++c) {
+            zj[c] = zrow[c * SH * SW + dx];
+            zs[c] = add_rn(zi[c], make_float2(zj[c], zj[c]));
+          }
+          float2 D;
+          if constexpr (METHOD == 0) {
+            D = det_adjugate<float2>(zs);
+          } else {
+            float xa[9], xb[9];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) xa[c] = zs[c].x, xb[c] = zs[c].y;
+            D = make_float2(det_cholesky(xa), det_cholesky(xb));
+          }
+          const float hj = hrow[dx];
+          const float ta = fmaxf(__log2f(D.x) - (kA + hj), 0.0f);
+          const float tb = fmaxf(__log2f(D.y) - (kB + hj), 0.0f);
+          if constexpr (DIST == kHellinger) {
+            // d_H = 1 - 2^(-L t), w = 2^(-(log2 e / h) d_H)
+            const float ha = 1.0f - exp2f(nl * ta), hb = 1.0f - exp2f(nl * tb);
+            w = mul_rn(make_float2(exp2f(nq * ha), exp2f(nq * hb)), m);
+          } else {
+            w = mul_rn(make_float2(exp2f(np * ta), exp2f(np * tb)), m);
+          }
         }
-        const float hj = hrow[dx];
-        const float ta = __log2f(D.x) - (kA + hj);
-        const float tb = __log2f(D.y) - (kB + hj);
-        const float2 w = mul_rn(make_float2(exp2f(np * fmaxf(ta, 0.0f)),
-                                            exp2f(np * fmaxf(tb, 0.0f))), m);
 #pragma unroll
         for (int c = 0; c < 9; ++c) acc[c] = fma_rn(w, make_float2(zj[c], zj[c]), acc[c]);
         ws = add_rn(ws, w);
@@ -156,11 +231,11 @@ __global__ void __launch_bounds__(kNT, 2) k_nlm(NlmArgs a) {
   }
 }
 
-template <int METHOD, int RAD>
+template <int METHOD, int RAD, int DIST>
 int launch_nlm(const NlmArgs& a, cudaStream_t s) {
   constexpr int SW = kNW + 2 * RAD, SH = kNH + 2 * RAD;
-  const size_t smem = (size_t)10 * SH * SW * sizeof(float);
-  auto k = k_nlm<METHOD, RAD>;
+  const size_t smem = (size_t)nlm_planes<DIST>() * SH * SW * sizeof(float);
+  auto k = k_nlm<METHOD, RAD, DIST>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
@@ -172,16 +247,16 @@ int launch_nlm(const NlmArgs& a, cudaStream_t s) {
   return launch_status();
 }
 
-template <int METHOD>
+template <int METHOD, int DIST>
 int dispatch_nlm(const NlmArgs& a, cudaStream_t s) {
   switch (a.radius) {
-    case 1: return launch_nlm<METHOD, 1>(a, s);
-    case 2: return launch_nlm<METHOD, 2>(a, s);
-    case 3: return launch_nlm<METHOD, 3>(a, s);
-    case 5: return launch_nlm<METHOD, 5>(a, s);
-    case 7: return launch_nlm<METHOD, 7>(a, s);
-    case 11: return launch_nlm<METHOD, 11>(a, s);
-    case 15: return launch_nlm<METHOD, 15>(a, s);
+    case 1: return launch_nlm<METHOD, 1, DIST>(a, s);
+    case 2: return launch_nlm<METHOD, 2, DIST>(a, s);
+    case 3: return launch_nlm<METHOD, 3, DIST>(a, s);
+    case 5: return launch_nlm<METHOD, 5, DIST>(a, s);
+    case 7: return launch_nlm<METHOD, 7, DIST>(a, s);
+    case 11: return launch_nlm<METHOD, 11, DIST>(a, s);
+    case 15: return launch_nlm<METHOD, 15, DIST>(a, s);
   }
   return ZINV_ERR_ARG;
 }
@@ -189,21 +264,41 @@ int dispatch_nlm(const NlmArgs& a, cudaStream_t s) {
 }  // namespace
 }  // namespace zinv
 
-extern "C" int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int radius,
-                           float looks, float h, int method, float* z_out, void* stream) {
+extern "C" int nlm_stochastic(const float* z, int64_t H, int64_t W, int64_t ld, int radius,
+                              float looks, float h, int distance, int method, float* z_out,
+                              void* stream) {
   using namespace zinv;
   if (H < 1 || W < 1 || H > kMaxLd / W || ld < H * W || ld > kMaxLd) return ZINV_ERR_ARG;
   if (radius != 1 && radius != 2 && radius != 3 && radius != 5 && radius != 7 &&
       radius != 11 && radius != 15)
     return ZINV_ERR_ARG;
   if (!(looks > 0.0f) || !(h > 0.0f) || isinf(looks) || isinf(h)) return ZINV_ERR_ARG;
+  if (distance != kBhattacharyya && distance != kHellinger && distance != kKullbackLeibler)
+    return ZINV_ERR_ARG;
   if (method != 0 && method != 1) return ZINV_ERR_ARG;
+  if (distance == kKullbackLeibler && method != 0) return ZINV_ERR_ARG;  // no pair det
   if (!z || !z_out || !aligned(z, 4) || !aligned(z_out, 4)) return ZINV_ERR_ARG;
   DeviceInfo di;
   int rc = device_info(&di);
   if (rc != ZINV_OK) return rc;
   if (!device_accessible(z) || !device_accessible(z_out)) return ZINV_ERR_ARG;
-  NlmArgs a{z, H, W, ld, radius, looks / h, z_out};
+  const double log2e = 1.44269504088896340736;
+  NlmArgs a{z, H, W, ld, radius, 0.0f, looks, (float)(log2e / h), z_out};
+  a.p = distance == kKullbackLeibler ? (float)(looks * log2e / h) : looks / h;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return method == 0 ? dispatch_nlm<0>(a, s) : dispatch_nlm<1>(a, s);
+  switch (distance) {
+    case kBhattacharyya:
+      return method == 0 ? dispatch_nlm<0, kBhattacharyya>(a, s)
+                         : dispatch_nlm<1, kBhattacharyya>(a, s);
+    case kHellinger:
+      return method == 0 ? dispatch_nlm<0, kHellinger>(a, s) : dispatch_nlm<1, kHellinger>(a, s);
+    default:
+      return dispatch_nlm<0, kKullbackLeibler>(a, s);
+  }
+}
+
+extern "C" int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int radius,
+                           float looks, float h, int method, float* z_out, void* stream) {
+  return nlm_stochastic(z, H, W, ld, radius, looks, h, zinv::kBhattacharyya, method, z_out,
+                        stream);
 }

@@ -154,3 +154,179 @@ def test_full_size_sampled(zlib, orc, method):
         k = (y - y0) * cw + (x - x0)
         bound = nlm_bound(crop, ch, cw, R, 16.0, ref_all)[:, k]
         check(out[:, y, x].cpu().numpy(), ref_all[:, k], bound, f"pixel {(y, x)}: ")
+
+
+# ---------------------------------------------------------------------------
+# nlm_stochastic: Hellinger and Kullback-Leibler weights
+# ---------------------------------------------------------------------------
+BHATTACHARYYA, HELLINGER, KULLBACK_LEIBLER = 0, 1, 2
+
+
+def inv3_with_magnitudes(Z):
+    """Exact (FP64) packed inverse of packed Z [9, ...], the magnitude sums S_k
+    of the three products in each cofactor of the compensated inverse (same
+    packed order), and the det with its expansion's magnitude sum E."""
+    a, br, bi, cr, ci, d, er, ei, f = Z
+    cof = np.stack([d * f - er * er - ei * ei, cr * er + ci * ei - br * f,
+                    ci * er - cr * ei - bi * f, br * er - bi * ei - cr * d,
+                    br * ei + bi * er - ci * d, a * f - cr * cr - ci * ci,
+                    cr * br + ci * bi - a * er, ci * br - cr * bi - a * ei,
+                    a * d - br * br - bi * bi])
+    A = np.abs
+    S = np.stack([A(d * f) + er * er + ei * ei, A(cr * er) + A(ci * ei) + A(br * f),
+                  A(ci * er) + A(cr * ei) + A(bi * f), A(br * er) + A(bi * ei) + A(cr * d),
+                  A(br * ei) + A(bi * er) + A(ci * d), A(a * f) + cr * cr + ci * ci,
+                  A(cr * br) + A(ci * bi) + A(a * er), A(ci * br) + A(cr * bi) + A(a * ei),
+                  A(a * d) + br * br + bi * bi])
+    det = det3(Z)
+    ab, ac, ae = A(br) + A(bi), A(cr) + A(ci), A(er) + A(ei)
+    E = a * (d * f + ae * ae) + ab * (ac * ae + ab * f) + ac * (ab * ae + ac * d)
+    return cof / det, S, det, E
+
+
+def stochastic_bound(z, H, W, radius, L, h, dist, ref):
+    """[9, H*W] first-order error bound of the FP32 filter with weights
+    w_ij = exp(-d_ij / h).  A relative error delta_ij of w_ij moves
+    Z'_i = sum_j w_ij Z_j / sum_j w_ij by at most
+        sum_j w_ij delta_ij |Z_jc - Z'_ic| / sum_j w_ij
+    (the exact weights from the FP64 distances), plus the FP32 rounding of the
+    two weighted sums, 2 gamma_(n_i + 2) max_j |Z_jc|.  Per pair:
+      Bhattacharyya   delta = (L/h) ln2 e + 2^-22, e the error of t as for nlm_wishart;
+      Hellinger       w = 2^(-(log2 e / h)(1 - x)), x = 2^(-L t) <= 1:
+                      delta = (L ln2 e + d_B u + 2^-22 + 3u) / h + 2^-22;
+      Kullback-Leibler  t = (tr(I_i Z_j) + tr(I_j Z_i)) / 2 - 3 with I the
+                      compensated inverse, |dI_k| <= 6u |I_k| + 2 gamma_3^2 (S_k + E |I_k|) / det
+                      (Dot2 cofactors and det), each trace a 9-term FP32 FMA chain
+                      (error <= sum c_k |dI_k| |Z_k| + gamma_9 sum c_k |I_k| |Z_k|,
+                      c_k = 2 off the diagonal), t rounded once more:
+                      e <= (dtr1 + dtr2 + u |tr1 + tr2|) / 2 + u |t|,
+                      delta = (L/h)(e + 2u t) + 2^-22.
+    The test bound is 1.25 times the total."""
+    Z = np.asarray(z, dtype=np.float64).reshape(9, H, W)
+    R = np.asarray(ref, dtype=np.float64).reshape(9, H, W)
+    hz = np.abs(np.log2(det3(Z))) / 2
+    ldz = np.log(det3(Z))
+    if dist == KULLBACK_LEIBLER:
+        I, S, dz, Ez = inv3_with_magnitudes(Z)
+        dI = 6 * U * np.abs(I) + 2 * gamma(3) ** 2 * (S + Ez * np.abs(I)) / dz
+        ck = np.array([1, 2, 2, 2, 2, 1, 2, 2, 1], dtype=np.float64)[:, None, None]
+    num = np.zeros((9, H, W))
+    den = np.zeros((H, W))
+    mag = np.zeros((9, H, W))
+    count = np.zeros((H, W))
+    for dy in range(-radius, radius + 1):
+        for dx in range(-radius, radius + 1):
+            ys = slice(max(0, -dy), min(H, H - dy))
+            xs = slice(max(0, -dx), min(W, W - dx))
+            yj = slice(max(0, dy), min(H, H + dy))
+            xj = slice(max(0, dx), min(W, W + dx))
+            zi, zj = Z[:, ys, xs], Z[:, yj, xj]
+            if dist == KULLBACK_LEIBLER:
+                Ii, Ij = I[:, ys, xs], I[:, yj, xj]
+                tr1 = (ck * Ii * zj).sum(axis=0)
+                tr2 = (ck * Ij * zi).sum(axis=0)
+                dtr1 = (ck * dI[:, ys, xs] * np.abs(zj)).sum(axis=0) \
+                    + gamma(9) * (ck * np.abs(Ii * zj)).sum(axis=0)
+                dtr2 = (ck * dI[:, yj, xj] * np.abs(zi)).sum(axis=0) \
+                    + gamma(9) * (ck * np.abs(Ij * zi)).sum(axis=0)
+                t = 0.5 * (tr1 + tr2) - 3
+                e = 0.5 * (dtr1 + dtr2 + U * np.abs(tr1 + tr2)) + U * np.abs(t)
+                delta = (L / h) * (e + 2 * U * np.abs(t)) + 2.0 ** -22
+                d = L * np.maximum(t, 0)
+            else:
+                s = zi + zj
+                a, br, bi, cr, ci, dd, er, ei, f = s
+                det = det3(s)
+                ab, ac, ae = np.abs(br) + np.abs(bi), np.abs(cr) + np.abs(ci), np.abs(er) + np.abs(ei)
+                E = a * (dd * f + ae * ae) + ab * (ac * ae + ab * f) + ac * (ab * ae + ac * dd)
+                e = (gamma(16) * E / (det * np.log(2)) + 2.0 ** -21
+                     + 4 * U * (np.abs(np.log2(det)) + 3 + hz[ys, xs] + hz[yj, xj]))
+                dB = L * np.maximum(np.log(det / 8) - 0.5 * (ldz[ys, xs] + ldz[yj, xj]), 0)
+                if dist == HELLINGER:
+                    delta = (L * np.log(2) * e + dB * U + 2.0 ** -22 + 3 * U) / h + 2.0 ** -22
+                    d = 1 - np.exp(-dB)
+                else:
+                    delta = (L / h) * np.log(2) * e + 2.0 ** -22
+                    d = dB
+            w = np.exp(-d / h)
+            num[:, ys, xs] += (w * delta)[None] * np.abs(zj - R[:, ys, xs])
+            den[ys, xs] += w
+            mag[:, ys, xs] = np.maximum(mag[:, ys, xs], np.abs(zj))
+            count[ys, xs] += 1
+    b = num / den[None] + 2 * gamma(count + 2)[None] * mag
+    return 1.25 * b.reshape(9, -1)
+
+
+def test_bhattacharyya_is_the_log_det_filter(zlib):
+    """nlm_stochastic with the Bhattacharyya distance runs nlm_wishart's kernel."""
+    H, W = 40, 75
+    w = S.scaled(S.WORKLOADS["scale_16k"], H, W)
+    z = torch.from_numpy(w.packed_z()).cuda().reshape(9, H, W)
+    for method in (0, 1):
+        a = zlib.nlm_wishart(z, 7, 16.0, 1.0, method)
+        b = zlib.nlm_stochastic(z, 7, 16.0, 1.0, BHATTACHARYYA, method)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("radius", [1, 3, 11])
+@pytest.mark.parametrize("dist,method,h", [(HELLINGER, 0, 0.25), (HELLINGER, 1, 0.25),
+                                           (KULLBACK_LEIBLER, 0, 4.0)])
+def test_stochastic_vs_oracle(zlib, orc, radius, dist, method, h):
+    """Every output pixel of a ragged 37 x 70 image (two partial tiles in x, a
+    ragged row pair) against the FP64 oracle under the derived bound.  The
+    Hellinger distance lies in [0, 1), so its h is smaller; both h move the
+    outputs by 10-20% of their scale (the filter does work)."""
+    H, W = 37, 70
+    w = S.scaled(S.WORKLOADS["scale_16k"], H, W)
+    z_np = w.packed_z()
+    z = torch.from_numpy(z_np).cuda().reshape(9, H, W)
+    out = zlib.nlm_stochastic(z, radius, 16.0, h, dist, method)
+    torch.cuda.synchronize()
+    ref = orc.nlm_stochastic(z_np, H, W, radius, 16.0, h, dist)
+    check(out.reshape(9, -1).cpu().numpy(), ref,
+          stochastic_bound(z_np, H, W, radius, 16.0, h, dist, ref))
+
+
+@pytest.mark.parametrize("dist,h", [(HELLINGER, 0.25), (KULLBACK_LEIBLER, 4.0)])
+def test_stochastic_full_size_sampled(zlib, orc, dist, h):
+    """The benchmark's 1024 x 1024 image, radius 11, in its launch
+    configuration: corner, edge and interior pixels against the oracle run on a
+    crop holding the pixel's search window."""
+    from paper_1807_08084_gb300.synth import gpu as G
+    R, N = 11, 1024
+    w = S.scaled(S.WORKLOADS["scale_16k"], N, N)
+    z = G.packed_z(w)
+    out = zlib.nlm_stochastic(z, R, 16.0, h, dist, 0).reshape(9, N, N)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(29)
+    pts = [(0, 0), (0, N - 1), (N - 1, 0), (N - 1, N - 1), (11, 511), (1012, 3)]
+    pts += [tuple(int(v) for v in rng.integers(R, N - R, 2)) for _ in range(6)]
+    for (y, x) in pts:
+        y0, y1, x0, x1 = max(0, y - R), min(N, y + R + 1), max(0, x - R), min(N, x + R + 1)
+        yy, xx = np.meshgrid(np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+        crop = w.packed_z((yy * N + xx).ravel().astype(np.uint64))
+        ch, cw = y1 - y0, x1 - x0
+        ref_all = orc.nlm_stochastic(crop, ch, cw, R, 16.0, h, dist)
+        k = (y - y0) * cw + (x - x0)
+        bound = stochastic_bound(crop, ch, cw, R, 16.0, h, dist, ref_all)[:, k]
+        check(out[:, y, x].cpu().numpy(), ref_all[:, k], bound, f"pixel {(y, x)}: ")
+
+
+@pytest.mark.parametrize("dist", [HELLINGER, KULLBACK_LEIBLER])
+def test_stochastic_constant_image_is_fixed_point(zlib, dist):
+    w = S.scaled(S.WORKLOADS["plain_256"], 1, 1)
+    z1 = torch.from_numpy(w.packed_z()).cuda()
+    z = z1.reshape(9, 1, 1).expand(9, 20, 30).contiguous()
+    out = zlib.nlm_stochastic(z, 5, 4.0, 0.5, dist, 0)
+    torch.cuda.synchronize()
+    # equal weights up to rounding of d near 0: the output is a weighted mean
+    # of one value, within 2 gamma_123 of it
+    assert torch.allclose(out, z, rtol=2 * gamma(123), atol=0)
+
+
+def test_stochastic_bad_arguments(zlib):
+    z = torch.zeros((9, 8, 8), device="cuda")
+    for dist, method in ((3, 0), (-1, 0), (KULLBACK_LEIBLER, 1), (HELLINGER, 2)):
+        with pytest.raises(RuntimeError):
+            zlib.nlm_stochastic(z, 3, 4.0, 1.0, dist, method)
