@@ -30,7 +30,10 @@
 // packed Hermitian products (nine FMAs each: tr(A B) = a a' + d d' + f f' +
 // 2 (Re b Re b' + Im b Im b' + ...)) and one exp2.
 //
-// Tiles of 32 x 16 outputs, 256 threads; each thread owns two vertically
+// Tiles of 32 x 16 outputs, 256 threads (Kullback-Leibler up to radius 11:
+// 32 x 32 outputs, 512 threads, as its 18 planes leave room for one CTA per
+// SM; 16 warps per SM instead of 8 took its 1024^2 launch from 1.155 to
+// 0.916 ms); each thread owns two vertically
 // adjacent outputs A and B, held as the two halves of packed f32x2 values:
 // every neighbour loaded from shared memory serves both outputs' pairs (one
 // packed sum Z_A + Z_j | Z_B + Z_j, one packed determinant by Algorithm 2, one
@@ -44,9 +47,8 @@
 namespace zinv {
 namespace {
 
-constexpr int kNT = 256;
 constexpr int kNW = 32;  // tile width
-constexpr int kNH = 16;  // tile height: 8 row pairs
+constexpr int kNH = 16;  // tile height: 8 row pairs, 256 threads
 
 // Distances (the values of nlm_stochastic's `distance`).
 constexpr int kBhattacharyya = 0, kHellinger = 1, kKullbackLeibler = 2;
@@ -66,6 +68,14 @@ template <int DIST>
 constexpr int nlm_planes() {
   return DIST == kKullbackLeibler ? 18 : 10;
 }
+
+// Tile height and threads: Kullback-Leibler's 18 planes leave room for one CTA
+// per SM, which then takes a 32 x 32 tile with 512 threads (radius <= 11).
+template <int RAD, int DIST>
+struct NlmTile {
+  static constexpr int TH = (DIST == kKullbackLeibler && RAD <= 11) ? 32 : kNH;
+  static constexpr int NT = kNW / 2 * TH;
+};
 
 // det by Algorithm 1's factorization: (l00 l11 l22)^2 with l00 = sqrt(a), the
 // first column scaled by 1/l00, l11 = sqrt(d - |l10|^2), l21 scaled by 1/l11,
@@ -87,21 +97,23 @@ __device__ __forceinline__ float det_cholesky(const float x[9]) {
 }
 
 template <int METHOD, int RAD, int DIST>
-__global__ void __launch_bounds__(kNT, 2) k_nlm(NlmArgs a) {
-  constexpr int SW = kNW + 2 * RAD, SH = kNH + 2 * RAD;
+__global__ void __launch_bounds__(NlmTile<RAD, DIST>::NT, 512 / NlmTile<RAD, DIST>::NT)
+    k_nlm(NlmArgs a) {
+  constexpr int TH = NlmTile<RAD, DIST>::TH, NT = NlmTile<RAD, DIST>::NT;
+  constexpr int SW = kNW + 2 * RAD, SH = TH + 2 * RAD;
   constexpr bool KL = DIST == kKullbackLeibler;
   extern __shared__ __align__(16) float smem[];
   float* Zs = smem;                // [9][SH][SW]
   float* Hs = smem + 9 * SH * SW;  // [SH][SW] half log2-dets, or [9][SH][SW] Z^-1 (KL)
   const int64_t n = a.H * a.W;
   const int64_t tiles_x = (a.W + kNW - 1) / kNW;
-  const int64_t tiles = tiles_x * ((a.H + kNH - 1) / kNH);
+  const int64_t tiles = tiles_x * ((a.H + TH - 1) / TH);
   const int tx = threadIdx.x % kNW, ty = 2 * (threadIdx.x / kNW);
   const float inv_ln2 = 1.44269504088896340736f;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t y0 = (t / tiles_x) * kNH, x0 = (t % tiles_x) * kNW;
+    const int64_t y0 = (t / tiles_x) * TH, x0 = (t % tiles_x) * kNW;
     __syncthreads();
-    for (int i = threadIdx.x; i < SH * SW; i += kNT) {
+    for (int i = threadIdx.x; i < SH * SW; i += NT) {
       const int sy = i / SW, sx = i - (i / SW) * SW;
       const int64_t gy = y0 - RAD + sy, gx = x0 - RAD + sx;
       if (gy < 0 || gy >= a.H || gx < 0 || gx >= a.W) continue;  // never read
@@ -233,7 +245,8 @@ __global__ void __launch_bounds__(kNT, 2) k_nlm(NlmArgs a) {
 
 template <int METHOD, int RAD, int DIST>
 int launch_nlm(const NlmArgs& a, cudaStream_t s) {
-  constexpr int SW = kNW + 2 * RAD, SH = kNH + 2 * RAD;
+  constexpr int TH = NlmTile<RAD, DIST>::TH, NT = NlmTile<RAD, DIST>::NT;
+  constexpr int SW = kNW + 2 * RAD, SH = TH + 2 * RAD;
   const size_t smem = (size_t)nlm_planes<DIST>() * SH * SW * sizeof(float);
   auto k = k_nlm<METHOD, RAD, DIST>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -241,9 +254,9 @@ int launch_nlm(const NlmArgs& a, cudaStream_t s) {
     cudaGetLastError();
     return ZINV_ERR_LAUNCH;
   }
-  const int64_t tiles = ((a.W + kNW - 1) / kNW) * ((a.H + kNH - 1) / kNH);
-  const int64_t blocks = cover_blocks(tiles * kNT, kNT);
-  k<<<(unsigned)blocks, kNT, smem, s>>>(a);
+  const int64_t tiles = ((a.W + kNW - 1) / kNW) * ((a.H + TH - 1) / TH);
+  const int64_t blocks = cover_blocks(tiles * NT, NT);
+  k<<<(unsigned)blocks, NT, smem, s>>>(a);
   return launch_status();
 }
 
