@@ -95,10 +95,11 @@ class Oracle:
         lib.oracle_nlm_wishart.argtypes = [_D, _I64, _I64, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, _D]
         lib.oracle_nlm_wishart.restype = None
-        lib.oracle_stochastic_distance.argtypes = [_D, _D, ctypes.c_double, ctypes.c_int]
+        lib.oracle_stochastic_distance.argtypes = [_D, _D, ctypes.c_double, ctypes.c_int,
+                                                   ctypes.c_double]
         lib.oracle_stochastic_distance.restype = ctypes.c_double
         lib.oracle_nlm_stochastic.argtypes = [_D, _I64, _I64, ctypes.c_int, ctypes.c_double,
-                                              ctypes.c_double, ctypes.c_int, _D]
+                                              ctypes.c_double, ctypes.c_int, ctypes.c_double, _D]
         lib.oracle_nlm_stochastic.restype = None
         for f in ("oracle_zinv_det", "oracle_det_expansions", "oracle_inverse_full",
                   "oracle_eigvals", "oracle_multilook", "oracle_zinv_det_bwd",
@@ -194,19 +195,21 @@ class Oracle:
         return out
 
     # -- stochastic distances between equal-looks Wishart laws (§1) ------
-    BHATTACHARYYA, HELLINGER, KULLBACK_LEIBLER = 0, 1, 2
+    BHATTACHARYYA, HELLINGER, KULLBACK_LEIBLER, RENYI = 0, 1, 2, 3
 
-    def stochastic_distance(self, zi, zj, looks: float, dist: int) -> float:
+    def stochastic_distance(self, zi, zj, looks: float, dist: int, order: float = 0.5) -> float:
         a, b = _f64(zi).reshape(9), _f64(zj).reshape(9)
-        return float(self.lib.oracle_stochastic_distance(_ptr(a), _ptr(b), float(looks), int(dist)))
+        return float(self.lib.oracle_stochastic_distance(_ptr(a), _ptr(b), float(looks),
+                                                         int(dist), float(order)))
 
     def nlm_stochastic(self, z, H: int, W: int, radius: int, looks: float, h: float,
-                       dist: int) -> np.ndarray:
-        """z: packed [9, H*W]; weights exp(-d / h) with the distance `dist`."""
+                       dist: int, order: float = 0.5) -> np.ndarray:
+        """z: packed [9, H*W]; weights exp(-d / h) with the distance `dist`
+        (`order`: the Renyi order in (0, 1))."""
         z = _f64(z).reshape(9, H * W)
         out = np.empty((9, H * W))
         self.lib.oracle_nlm_stochastic(_ptr(z), H, W, int(radius), float(looks), float(h),
-                                       int(dist), _ptr(out))
+                                       int(dist), float(order), _ptr(out))
         return out
 
     # -- Wishart change statistic ----------------------------------------

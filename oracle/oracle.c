@@ -48,7 +48,7 @@
  *                          h -> 0 (identity), d >= 0 with d(i, i) = 0 and
  *                          symmetry, and brute-force numpy.
  *   oracle_stochastic_distance, oracle_nlm_stochastic
- *                          Bhattacharyya, Hellinger and Kullback-Leibler distances
+ *                          Bhattacharyya, Hellinger, Kullback-Leibler and Renyi distances
  *                          between equal-looks complex Wishart laws (§1's list of
  *                          divergences), in closed form from the Wishart density,
  *                          and the nonlocal-means filter weighted by exp(-d / h).
@@ -756,14 +756,19 @@ void oracle_nlm_wishart(const double* z, int64_t H, int64_t W, int radius, doubl
 /*                           + (ln det S_i + ln det S_j)/2],                 */
 /*   Hellinger      d_H = 1 - that integral = 1 - exp(-d_B),                 */
 /*   Kullback-Leibler (the mean of the two directed divergences)             */
-/*                  d_KL = L [(tr(S_i^-1 S_j) + tr(S_j^-1 S_i))/2 - m].      */
-/* All three are >= 0, symmetric, and 0 iff S_i = S_j.  The oracle takes     */
+/*                  d_KL = L [(tr(S_i^-1 S_j) + tr(S_j^-1 S_i))/2 - m],      */
+/*   Renyi of order b in (0, 1) (the mean of the two directed divergences    */
+/*   D_b(i||j) = ln(integral of f_i^b f_j^(1-b)) / (b - 1))                  */
+/*                  D_b(i||j) = L/(1-b) [ln det(b S_i^-1 + (1-b) S_j^-1)     */
+/*                                       + b ln det S_i + (1-b) ln det S_j]. */
+/* All four are >= 0, symmetric, and 0 iff S_i = S_j.  The oracle takes      */
 /* them as written, with Gauss-Jordan inverses and elimination dets.         */
 /* ------------------------------------------------------------------------ */
 
 #define ORACLE_DIST_BHATTACHARYYA 0
 #define ORACLE_DIST_HELLINGER 1
 #define ORACLE_DIST_KULLBACK_LEIBLER 2
+#define ORACLE_DIST_RENYI 3
 
 /* tr(X Y) = sum_r sum_c X[r][c] Y[c][r] (real for Hermitian X, Y). */
 static double trace_of_product(const mat3* X, const mat3* Y)
@@ -779,13 +784,32 @@ static double trace_of_product(const mat3* X, const mat3* Y)
     return creal(t);
 }
 
+/* Directed Renyi divergence of order b of W(S_x, L) from W(S_y, L), from the
+ * inverses Ix, Iy and log-dets of S_x, S_y. */
+static double renyi_directed(const mat3* Ix, const mat3* Iy, double ldx, double ldy,
+                             double looks, double b)
+{
+    mat3 A;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+#if ORACLE_MUTANT == 15
+            A.m[r][c] = b * (Ix->m[r][c] + Iy->m[r][c]); /* mutant: b on both terms */
+#else
+            A.m[r][c] = b * Ix->m[r][c] + (1.0 - b) * Iy->m[r][c];
+#endif
+    return looks / (1.0 - b) * (logdet(&A) + b * ldx + (1.0 - b) * ldy);
+}
+
 /* One pixel pair, given both covariances, their inverses and log-dets. */
 static double stochastic_distance(const mat3* Si, const mat3* Sj, const mat3* Ii,
                                   const mat3* Ij, double ldi, double ldj, double looks,
-                                  int dist)
+                                  int dist, double order)
 {
     if (dist == ORACLE_DIST_KULLBACK_LEIBLER)
         return looks * (0.5 * (trace_of_product(Ii, Sj) + trace_of_product(Ij, Si)) - 3.0);
+    if (dist == ORACLE_DIST_RENYI)
+        return 0.5 * (renyi_directed(Ii, Ij, ldi, ldj, looks, order) +
+                      renyi_directed(Ij, Ii, ldj, ldi, looks, order));
     mat3 M;
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) M.m[r][c] = 0.5 * (Ii->m[r][c] + Ij->m[r][c]);
@@ -799,21 +823,25 @@ static double stochastic_distance(const mat3* Si, const mat3* Sj, const mat3* Ii
     return dB;
 }
 
-/* d(S_i, S_j) for packed zi, zj (nine doubles each); NaN for an unknown dist
- * or a singular matrix. */
-double oracle_stochastic_distance(const double* zi, const double* zj, double looks, int dist)
+/* d(S_i, S_j) for packed zi, zj (nine doubles each); `order` is the Renyi
+ * order b in (0, 1), unused by the other distances.  NaN for an unknown dist,
+ * an order outside (0, 1) for Renyi, or a singular matrix. */
+double oracle_stochastic_distance(const double* zi, const double* zj, double looks, int dist,
+                                  double order)
 {
-    if (dist < 0 || dist > 2) return NAN;
+    if (dist < 0 || dist > 3) return NAN;
+    if (dist == ORACLE_DIST_RENYI && !(order > 0.0 && order < 1.0)) return NAN;
     mat3 Si = unpack(zi, 1, 0), Sj = unpack(zj, 1, 0), Ii, Ij;
     if (ge_inverse(&Si, &Ii) || ge_inverse(&Sj, &Ij)) return NAN;
-    return stochastic_distance(&Si, &Sj, &Ii, &Ij, logdet(&Si), logdet(&Sj), looks, dist);
+    return stochastic_distance(&Si, &Sj, &Ii, &Ij, logdet(&Si), logdet(&Sj), looks, dist,
+                               order);
 }
 
 /* Nonlocal means with weights w_ij = exp(-d(i, j) / h) over the in-image
  * neighbours within the search radius (d including the factor L); the
  * Bhattacharyya case equals oracle_nlm_wishart. */
 void oracle_nlm_stochastic(const double* z, int64_t H, int64_t W, int radius, double looks,
-                           double h, int dist, double* out)
+                           double h, int dist, double order, double* out)
 {
     int64_t n = H * W;
     mat3* inv = (mat3*)malloc((size_t)n * sizeof(mat3));
@@ -835,7 +863,7 @@ void oracle_nlm_stochastic(const double* z, int64_t H, int64_t W, int radius, do
                     int64_t j = yy * W + xx;
                     mat3 Sj = unpack(z, n, j);
                     double d = stochastic_distance(&Si, &Sj, &inv[i], &inv[j], ld[i], ld[j],
-                                                   looks, dist);
+                                                   looks, dist, order);
                     double w = exp(-d / h);
                     for (int k = 0; k < 9; ++k) acc[k] += w * z[k * n + j];
                     wsum += w;

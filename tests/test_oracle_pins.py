@@ -17,8 +17,8 @@ not agree with what the paper and the mathematics fix:
 * q <= 0, q(Z, Z) = 0, Euler homogeneity and date-swap symmetry for the Wishart
   change statistic;
 * Monte Carlo estimates, from sampled complex Wishart matrices, of the integrals
-  that define the Bhattacharyya and Kullback-Leibler distances, and the
-  closed forms and invariances of those distances.
+  that define the Bhattacharyya, Kullback-Leibler and Renyi distances, and the
+  closed forms, limits and invariances of those distances.
 
 ``test_mutants_are_caught`` builds the oracle with each planted mistake and
 requires that at least one check fails for each.
@@ -388,11 +388,18 @@ def check_stochastic_distances(o):
     to the density they are defined from and to the mathematics, not to their
     closed forms alone."""
     from paper_1807_08084_gb300 import synth as S
-    B, HL, KL = o.BHATTACHARYYA, o.HELLINGER, o.KULLBACK_LEIBLER
+    B, HL, KL, RY = o.BHATTACHARYYA, o.HELLINGER, o.KULLBACK_LEIBLER, o.RENYI
     rng = np.random.default_rng(23)
     L = 4.0
     Z = pack(random_pd(rng, 40, cond_max=1e2))
     A = unpack(Z)
+
+    def renyi_z_form(Si, Sj, b):
+        """(D_b(i||j) + D_b(j||i)) / 2 through det((1-b) S_x + b S_y) (numpy)."""
+        ldi, ldj = np.linalg.slogdet(Si)[1], np.linalg.slogdet(Sj)[1]
+        dij = np.linalg.slogdet((1 - b) * Si + b * Sj)[1] - (1 - b) * ldi - b * ldj
+        dji = np.linalg.slogdet((1 - b) * Sj + b * Si)[1] - (1 - b) * ldj - b * ldi
+        return L / (1 - b) * 0.5 * (dij + dji)
     for k in range(0, 40, 2):
         zi, zj = Z[:, k], Z[:, k + 1]
         dB, dH, dK = (o.stochastic_distance(zi, zj, L, d) for d in (B, HL, KL))
@@ -409,6 +416,21 @@ def check_stochastic_distances(o):
         ti, tj = pack(T @ A[k] @ T.conj().T), pack(T @ A[k + 1] @ T.conj().T)
         for d, v in ((B, dB), (HL, dH), (KL, dK)):
             assert abs(o.stochastic_distance(ti, tj, L, d) - v) < 1e-8 * max(1.0, v)
+        # Renyi: order 1/2 is twice Bhattacharyya, order -> 1 tends to KL, the
+        # inverse form (the oracle) equals the Z form (numpy), symmetric,
+        # invariant, zero on the diagonal
+        assert abs(o.stochastic_distance(zi, zj, L, RY, 0.5) - 2 * dB) < 1e-11 * max(1.0, dB)
+        # D_b = D_KL + c1 (1 - b) + c2 (1 - b)^2 + ...: one Richardson step
+        # removes the linear term (c2 reaches ~5e7 for the most distant pair)
+        ext = (2 * o.stochastic_distance(zi, zj, L, RY, 1 - 1e-7)
+               - o.stochastic_distance(zi, zj, L, RY, 1 - 2e-7))
+        assert abs(ext - dK) < 1e-6 * max(1.0, dK)
+        for b in (0.2, 0.75):
+            v = o.stochastic_distance(zi, zj, L, RY, b)
+            assert v > 0 and abs(v - renyi_z_form(A[k], A[k + 1], b)) < 1e-10 * max(1.0, v)
+            assert abs(o.stochastic_distance(zj, zi, L, RY, b) - v) < 1e-12 * max(1.0, v)
+            assert abs(o.stochastic_distance(zi, zi, L, RY, b)) < 1e-12
+            assert abs(o.stochastic_distance(ti, tj, L, RY, b) - v) < 1e-8 * max(1.0, v)
         # KL against numpy: traces of S_i^-1 S_j
         ref = L * (0.5 * (np.trace(np.linalg.solve(A[k], A[k + 1]))
                           + np.trace(np.linalg.solve(A[k + 1], A[k]))).real - 3)
@@ -420,6 +442,11 @@ def check_stochastic_distances(o):
         assert abs(o.stochastic_distance(zi, c * zi, L, B) - dB) < 1e-12
         assert abs(o.stochastic_distance(zi, c * zi, L, HL) - (1 - np.exp(-dB))) < 1e-12
         assert abs(o.stochastic_distance(zi, c * zi, L, KL) - 3 * L * ((c + 1 / c) / 2 - 1)) < 1e-12
+        for b in (0.3, 0.75):
+            dij = 3 * (np.log(1 - b + b * c) - b * np.log(c))
+            dji = 3 * (np.log(1 - b + b / c) + b * np.log(c))
+            assert abs(o.stochastic_distance(zi, c * zi, L, RY, b)
+                       - L / (1 - b) * 0.5 * (dij + dji)) < 1e-12
     a, b = np.array([1.0, 0.3, 7.0]), np.array([2.0, 0.3, 0.5])
     za, zb = np.zeros(9), np.zeros(9)
     za[[0, 5, 8]], zb[[0, 5, 8]] = a, b
@@ -447,6 +474,14 @@ def check_stochastic_distances(o):
     kl = 0.5 * (np.mean(-lr["ij"]) + np.mean(-lr["ji"]))
     se_kl = 0.5 * (lr["ij"].std() + lr["ji"].std()) / np.sqrt(n)
     assert abs(o.stochastic_distance(zi, zj, Li, KL) - kl) < 5 * se_kl
+    # Renyi: the integral of f_i^b f_j^(1-b) is E_i[(f_j / f_i)^(1-b)]
+    b = 0.7
+    ry, var = 0.0, 0.0
+    for key in ("ij", "ji"):
+        m = np.exp((1 - b) * lr[key])
+        ry += 0.5 * np.log(m.mean()) / (b - 1)
+        var += (0.5 / (1 - b) * m.std() / m.mean()) ** 2 / n
+    assert abs(o.stochastic_distance(zi, zj, Li, RY, b) - ry) < 5 * np.sqrt(var) + 1e-3 * ry
     # the filters: Bhattacharyya weights are the log-det filter's; Hellinger
     # and Kullback-Leibler against a numpy brute force on a tiny image
     H, W, rad, h = 6, 7, 2, 0.8
@@ -457,8 +492,8 @@ def check_stochastic_distances(o):
     Az = unpack(z)
     inv = np.linalg.inv(Az)
     ld = np.linalg.slogdet(Az)[1]
-    for dist in (HL, KL):
-        out = o.nlm_stochastic(z, H, W, rad, L, h, dist)
+    for dist in (HL, KL, RY):
+        out = o.nlm_stochastic(z, H, W, rad, L, h, dist, 0.7)
         ref = np.empty_like(out)
         for y in range(H):
             for x in range(W):
@@ -469,6 +504,8 @@ def check_stochastic_distances(o):
                         j = yy * W + xx
                         if dist == KL:
                             d = L * (0.5 * np.trace(inv[i] @ Az[j] + inv[j] @ Az[i]).real - 3)
+                        elif dist == RY:
+                            d = renyi_z_form(Az[i], Az[j], 0.7)
                         else:
                             d = 1 - np.exp(-L * (np.linalg.slogdet((inv[i] + inv[j]) / 2)[1]
                                                  + 0.5 * (ld[i] + ld[j])))
@@ -507,6 +544,7 @@ MUTANTS = {
     12: "nonlocal means drops the 1/2 of the pair mean",
     13: "trace of a product takes the second factor untransposed",
     14: "Hellinger distance from the square root of the Bhattacharyya coefficient",
+    15: "Renyi divergence weights both inverses by the order",
 }
 
 
