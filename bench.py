@@ -632,7 +632,7 @@ def main():
                            "(23 x 23 window), L = 16, h = 1")
         # the other stochastic distances (nlm_stochastic): Hellinger shares the
         # per-pair determinant; Kullback-Leibler takes two traces with the
-        # per-pixel inverses instead
+        # per-pixel inverses instead; Renyi two determinants per pair
         hel = {}
         for name, meth in (("adjugate", zp.NLM_ADJUGATE), ("cholesky", zp.NLM_CHOLESKY)):
             t = timed(lambda: zp.nlm_stochastic(zn, 11, 16.0, 0.25, zp.NLM_HELLINGER, meth,
@@ -645,6 +645,14 @@ def main():
                                             zp.NLM_ADJUGATE, out=zo), max(3, sub // 5),
                   args.warmup, world)
         nlm["kullback_leibler"] = {"ms": t, "gpairs_s": pairs / (t * 1e-3) / 1e9, "h": 4.0}
+        ren = {}
+        for name, meth in (("adjugate", zp.NLM_ADJUGATE), ("cholesky", zp.NLM_CHOLESKY)):
+            t = timed(lambda: zp.nlm_stochastic(zn, 11, 16.0, 2.0, zp.NLM_RENYI, meth, out=zo,
+                                                order=0.7), max(3, sub // 5), args.warmup, world)
+            ren[name] = {"ms": t, "gpairs_s": pairs / (t * 1e-3) / 1e9}
+        ren["speedup_adjugate_vs_cholesky"] = ren["cholesky"]["ms"] / ren["adjugate"]["ms"]
+        ren["h"], ren["order"] = 2.0, 0.7
+        nlm["renyi"] = ren
         del zn, zo
 
     # --- Wishart change statistic (two 4096 x 4096 dates, 7 x 7 window) -------

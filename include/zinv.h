@@ -208,21 +208,29 @@ int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int radius, fl
  *   ZINV_NLM_KULLBACK_LEIBLER d = L [(tr(Z_i^-1 Z_j) + tr(Z_j^-1 Z_i))/2 - 3], the mean
  *                             of the two directed divergences; Z^-1 of every pixel
  *                             by Algorithm 2 (compensated cofactors and det).
- *   method    the per-pair determinant of Bhattacharyya and Hellinger:
+ *   ZINV_NLM_RENYI            d = L/(1-b) [(ln det((1-b) Z_i + b Z_j) + ln det(b Z_i
+ *                             + (1-b) Z_j))/2 - (ln det Z_i + ln det Z_j)/2], the mean
+ *                             of the two directed divergences of order b = `order`
+ *                             (b = 1/2 gives twice the Bhattacharyya distance; b -> 1
+ *                             tends to Kullback-Leibler); two determinants per pair.
+ *   order     the Renyi order b, in (0, 1); unused by the other distances.
+ *   method    the per-pair determinants of Bhattacharyya, Hellinger and Renyi:
  *             ZINV_NLM_ADJUGATE (Algorithm 2) or ZINV_NLM_CHOLESKY (Algorithm 1).
  *             Kullback-Leibler takes no per-pair determinant and accepts
  *             ZINV_NLM_ADJUGATE only.
  *   z, H, W, ld, radius, looks, h, z_out, stream  as nlm_wishart.
- * Returns ZINV_ERR_ARG for an unknown distance or method, or a method the
- * distance does not take, before any device work.
+ * Returns ZINV_ERR_ARG for an unknown distance or method, a method the
+ * distance does not take, or a Renyi order outside (0, 1), before any device
+ * work.
  */
 #define ZINV_NLM_ADJUGATE 0
 #define ZINV_NLM_CHOLESKY 1
 #define ZINV_NLM_BHATTACHARYYA 0
 #define ZINV_NLM_HELLINGER 1
 #define ZINV_NLM_KULLBACK_LEIBLER 2
+#define ZINV_NLM_RENYI 3
 int nlm_stochastic(const float* z, int64_t H, int64_t W, int64_t ld, int radius, float looks,
-                   float h, int distance, int method, float* z_out, void* stream);
+                   float h, int distance, float order, int method, float* z_out, void* stream);
 
 /*
  * Wishart change statistic between two dates with a learnable window (the

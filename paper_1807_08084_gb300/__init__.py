@@ -80,7 +80,8 @@ def _declare_extra(lib):
                                 ctypes.c_float, ctypes.c_int, _P, _P]
     lib.nlm_wishart.restype = ctypes.c_int
     lib.nlm_stochastic.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_float,
-                                   ctypes.c_float, ctypes.c_int, ctypes.c_int, _P, _P]
+                                   ctypes.c_float, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                   _P, _P]
     lib.nlm_stochastic.restype = ctypes.c_int
     lib.wishart_workspace_bytes.argtypes = [_I64, _I64, ctypes.c_int]
     lib.wishart_workspace_bytes.restype = ctypes.c_size_t
@@ -313,15 +314,17 @@ def nlm_wishart(z: torch.Tensor, radius: int = 11, looks: float = 16.0, h: float
 NLM_BHATTACHARYYA = 0
 NLM_HELLINGER = 1
 NLM_KULLBACK_LEIBLER = 2
+NLM_RENYI = 3
 
 
 def nlm_stochastic(z: torch.Tensor, radius: int = 11, looks: float = 16.0, h: float = 1.0,
                    distance: int = NLM_BHATTACHARYYA, method: int = NLM_ADJUGATE,
-                   out: torch.Tensor | None = None) -> torch.Tensor:
+                   out: torch.Tensor | None = None, order: float = 0.5) -> torch.Tensor:
     """Nonlocal-means filter of a packed [9, H, W] image with weights
-    exp(-d / h), d the Bhattacharyya, Hellinger or Kullback-Leibler distance
-    between the pixels' equal-looks Wishart laws; the per-pair determinant of
-    the first two by Algorithm 2 (NLM_ADJUGATE) or Algorithm 1 (NLM_CHOLESKY)."""
+    exp(-d / h), d the Bhattacharyya, Hellinger, Kullback-Leibler or Renyi
+    (of `order` in (0, 1)) distance between the pixels' equal-looks Wishart
+    laws; the per-pair determinants by Algorithm 2 (NLM_ADJUGATE) or
+    Algorithm 1 (NLM_CHOLESKY), Kullback-Leibler taking none."""
     lib = load()
     if z.dim() != 3:
         raise ValueError("z must be [9, H, W]")
@@ -333,7 +336,8 @@ def nlm_stochastic(z: torch.Tensor, radius: int = 11, looks: float = 16.0, h: fl
         _out(out, (9, H, W), z.device, "out")
     with torch.cuda.device(z.device):
         rc = lib.nlm_stochastic(_ptr(z), H, W, ld, int(radius), float(looks), float(h),
-                                int(distance), int(method), _ptr(out), _stream(z.device))
+                                int(distance), float(order), int(method), _ptr(out),
+                                _stream(z.device))
     _check(rc, "nlm_stochastic")
     return out
 

@@ -12,7 +12,10 @@
 //                  as Z_i^-1 + Z_j^-1 = Z_i^-1 (Z_i + Z_j) Z_j^-1),
 //   Hellinger      d_H = 1 - exp(-d_B),
 //   Kullback-Leibler (mean of both directions)
-//                  d_KL = L [(tr(Z_i^-1 Z_j) + tr(Z_j^-1 Z_i))/2 - 3].
+//                  d_KL = L [(tr(Z_i^-1 Z_j) + tr(Z_j^-1 Z_i))/2 - 3],
+//   Renyi of order b in (0, 1) (mean of both directions)
+//                  d_R = L/(1-b) [(ln det((1-b) Z_i + b Z_j) + ln det(b Z_i + (1-b) Z_j))/2
+//                                 - (ln det Z_i + ln det Z_j)/2].
 //
 // Bhattacharyya and Hellinger, in base 2 with D_ij = det(Z_i + Z_j) and
 // h_i = log2(det Z_i) / 2:  d_B = L ln2 t_ij,  t_ij = max(log2 D_ij - (3 + h_i) - h_j, 0)
@@ -25,6 +28,10 @@
 // Algorithm 1's Cholesky route (three square roots, two reciprocals);
 // everything else is shared, so the two can be compared where arithmetic, not
 // memory, sets the time.
+// Renyi: the same staging; per pair the two convex combinations (1-b) Z_A +
+// b Z_j and b Z_A + (1-b) Z_j (packed FMAs from the pre-scaled own matrices),
+// both determinants by Algorithm 2 or 1, and w = 2^(-(L/((1-b) h)) t) with
+// t = max((log2 D1 + log2 D2)/2 - h_i - h_j, 0).
 // Kullback-Leibler: Z^-1 of every staged pixel by Algorithm 2 with compensated
 // (Dot2) cofactors and det, once per staged pixel; per pair two traces of
 // packed Hermitian products (nine FMAs each: tr(A B) = a a' + d d' + f f' +
@@ -51,15 +58,16 @@ constexpr int kNW = 32;  // tile width
 constexpr int kNH = 16;  // tile height: 8 row pairs, 256 threads
 
 // Distances (the values of nlm_stochastic's `distance`).
-constexpr int kBhattacharyya = 0, kHellinger = 1, kKullbackLeibler = 2;
+constexpr int kBhattacharyya = 0, kHellinger = 1, kKullbackLeibler = 2, kRenyi = 3;
 
 struct NlmArgs {
   const float* z;
   int64_t H, W, ld;
   int radius;
-  float p;      // Bhattacharyya: L / h; Kullback-Leibler: L log2(e) / h
+  float p;      // Bhattacharyya: L / h; Kullback-Leibler: L log2(e) / h; Renyi: L / ((1-b) h)
   float looks;  // Hellinger: L
   float qh;     // Hellinger: log2(e) / h
+  float b, b1;  // Renyi: the order b and 1 - b
   float* out;
 };
 
@@ -149,8 +157,19 @@ __global__ void __launch_bounds__(NlmTile<RAD, DIST>::NT, 512 / NlmTile<RAD, DIS
       acc[c] = make_float2(0.0f, 0.0f);
     }
     float2 ii2[KL ? 9 : 1], zi2[KL ? 9 : 1];
+    constexpr bool RY = DIST == kRenyi;
+    float2 zb1[RY ? 9 : 1], zb[RY ? 9 : 1];  // Renyi: (1-b) Z and b Z of A | B
     float kA = 0.0f, kB = 0.0f;
-    if constexpr (KL) {
+    if constexpr (RY) {
+      const float2 b2 = make_float2(a.b, a.b), b12 = make_float2(a.b1, a.b1);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        zb1[c] = mul_rn(b12, zi[c]);
+        zb[c] = mul_rn(b2, zi[c]);
+      }
+      kA = Hs[cy * SW + cx];
+      kB = hasB ? Hs[(cy + 1) * SW + cx] : kA;
+    } else if constexpr (KL) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         const float two = (c == 0 || c == 5 || c == 8) ? 1.0f : 2.0f;
@@ -199,6 +218,30 @@ __global__ void __launch_bounds__(NlmTile<RAD, DIST>::NT, 512 / NlmTile<RAD, DIS
                                    make_float2(-3.0f, -3.0f));
           w = mul_rn(make_float2(exp2f(np * fmaxf(tk.x, 0.0f)), exp2f(np * fmaxf(tk.y, 0.0f))),
                      m);
+        } else if constexpr (RY) {
+          float2 m1[9], m2[9];
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            zj[c] = zrow[c * SH * SW + dx];
+            m1[c] = fma_rn(make_float2(a.b, a.b), make_float2(zj[c], zj[c]), zb1[c]);
+            m2[c] = fma_rn(make_float2(a.b1, a.b1), make_float2(zj[c], zj[c]), zb[c]);
+          }
+          float2 D1, D2;
+          if constexpr (METHOD == 0) {
+            D1 = det_adjugate<float2>(m1);
+            D2 = det_adjugate<float2>(m2);
+          } else {
+            float x1[9], x2[9], x3[9], x4[9];
+#pragma unroll
+            for (int c = 0; c < 9; ++c)
+              x1[c] = m1[c].x, x2[c] = m1[c].y, x3[c] = m2[c].x, x4[c] = m2[c].y;
+            D1 = make_float2(det_cholesky(x1), det_cholesky(x2));
+            D2 = make_float2(det_cholesky(x3), det_cholesky(x4));
+          }
+          const float hj = hrow[dx];
+          const float ta = fmaxf(0.5f * (__log2f(D1.x) + __log2f(D2.x)) - (kA + hj), 0.0f);
+          const float tb = fmaxf(0.5f * (__log2f(D1.y) + __log2f(D2.y)) - (kB + hj), 0.0f);
+          w = mul_rn(make_float2(exp2f(np * ta), exp2f(np * tb)), m);
         } else {
           float2 zs[9];
 #pragma unroll
@@ -278,16 +321,18 @@ int dispatch_nlm(const NlmArgs& a, cudaStream_t s) {
 }  // namespace zinv
 
 extern "C" int nlm_stochastic(const float* z, int64_t H, int64_t W, int64_t ld, int radius,
-                              float looks, float h, int distance, int method, float* z_out,
-                              void* stream) {
+                              float looks, float h, int distance, float order, int method,
+                              float* z_out, void* stream) {
   using namespace zinv;
   if (H < 1 || W < 1 || H > kMaxLd / W || ld < H * W || ld > kMaxLd) return ZINV_ERR_ARG;
   if (radius != 1 && radius != 2 && radius != 3 && radius != 5 && radius != 7 &&
       radius != 11 && radius != 15)
     return ZINV_ERR_ARG;
   if (!(looks > 0.0f) || !(h > 0.0f) || isinf(looks) || isinf(h)) return ZINV_ERR_ARG;
-  if (distance != kBhattacharyya && distance != kHellinger && distance != kKullbackLeibler)
+  if (distance != kBhattacharyya && distance != kHellinger && distance != kKullbackLeibler &&
+      distance != kRenyi)
     return ZINV_ERR_ARG;
+  if (distance == kRenyi && !(order > 0.0f && order < 1.0f)) return ZINV_ERR_ARG;
   if (method != 0 && method != 1) return ZINV_ERR_ARG;
   if (distance == kKullbackLeibler && method != 0) return ZINV_ERR_ARG;  // no pair det
   if (!z || !z_out || !aligned(z, 4) || !aligned(z_out, 4)) return ZINV_ERR_ARG;
@@ -296,8 +341,13 @@ extern "C" int nlm_stochastic(const float* z, int64_t H, int64_t W, int64_t ld, 
   if (rc != ZINV_OK) return rc;
   if (!device_accessible(z) || !device_accessible(z_out)) return ZINV_ERR_ARG;
   const double log2e = 1.44269504088896340736;
-  NlmArgs a{z, H, W, ld, radius, 0.0f, looks, (float)(log2e / h), z_out};
+  NlmArgs a{z, H, W, ld, radius, 0.0f, looks, (float)(log2e / h), 0.0f, 0.0f, z_out};
   a.p = distance == kKullbackLeibler ? (float)(looks * log2e / h) : looks / h;
+  if (distance == kRenyi) {
+    a.b = order;
+    a.b1 = (float)(1.0 - (double)order);
+    a.p = (float)((double)looks / ((1.0 - (double)order) * (double)h));
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (distance) {
     case kBhattacharyya:
@@ -305,6 +355,8 @@ extern "C" int nlm_stochastic(const float* z, int64_t H, int64_t W, int64_t ld, 
                          : dispatch_nlm<1, kBhattacharyya>(a, s);
     case kHellinger:
       return method == 0 ? dispatch_nlm<0, kHellinger>(a, s) : dispatch_nlm<1, kHellinger>(a, s);
+    case kRenyi:
+      return method == 0 ? dispatch_nlm<0, kRenyi>(a, s) : dispatch_nlm<1, kRenyi>(a, s);
     default:
       return dispatch_nlm<0, kKullbackLeibler>(a, s);
   }
@@ -312,6 +364,6 @@ extern "C" int nlm_stochastic(const float* z, int64_t H, int64_t W, int64_t ld, 
 
 extern "C" int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int radius,
                            float looks, float h, int method, float* z_out, void* stream) {
-  return nlm_stochastic(z, H, W, ld, radius, looks, h, zinv::kBhattacharyya, method, z_out,
-                        stream);
+  return nlm_stochastic(z, H, W, ld, radius, looks, h, zinv::kBhattacharyya, 0.5f, method,
+                        z_out, stream);
 }

@@ -84,11 +84,15 @@ def test_host_argument_checks():
     assert lib.zinv_det_host(P(fake), 10, 10, P(fake), P(fake), 0, 0.0, P(fake + 16), 1 << 20,
                              None) == -1  # workspace not 256-byte aligned
     z9 = P(fake)
-    for dist, method in ((3, 0), (-1, 0), (2, 1), (1, 2)):  # unknown, or KL with Cholesky
-        assert lib.nlm_stochastic(z9, 10, 10, 100, 3, 4.0, 1.0, dist, method, z9, None) == -1
-    assert lib.nlm_stochastic(z9, 10, 10, 100, 4, 4.0, 1.0, 0, 0, z9, None) == -1  # radius
-    for dist, method in ((0, 0), (1, 1), (2, 0)):
-        assert lib.nlm_stochastic(z9, 10, 10, 100, 3, 4.0, 1.0, dist, method, z9, None) == -3
+    # unknown distance, KL with Cholesky, unknown method, Renyi order outside (0, 1)
+    for dist, order, method in ((4, 0.5, 0), (-1, 0.5, 0), (2, 0.5, 1), (1, 0.5, 2),
+                                (3, 0.0, 0), (3, 1.0, 0), (3, float("nan"), 1)):
+        assert lib.nlm_stochastic(z9, 10, 10, 100, 3, 4.0, 1.0, dist, order, method, z9,
+                                  None) == -1
+    assert lib.nlm_stochastic(z9, 10, 10, 100, 4, 4.0, 1.0, 0, 0.5, 0, z9, None) == -1  # radius
+    for dist, method in ((0, 0), (1, 1), (2, 0), (3, 1)):
+        assert lib.nlm_stochastic(z9, 10, 10, 100, 3, 4.0, 1.0, dist, 0.5, method, z9,
+                                  None) == -3
     assert lib.zinv_det_host_workspace_bytes(0) == 0
     assert lib.zinv_det_host_workspace_bytes(1024) >= 3 * 40 * 1024
 

@@ -152,17 +152,17 @@ def test_nlm_output(zlib, radius, method):
     out.check(f"nlm radius {radius} method {method}")
 
 
-@pytest.mark.parametrize("dist,method", [(1, 0), (1, 1), (2, 0)])
+@pytest.mark.parametrize("dist,method", [(1, 0), (1, 1), (2, 0), (3, 0), (3, 1)])
 @pytest.mark.parametrize("radius", [2, 11, 15])
 def test_nlm_stochastic_output(zlib, radius, dist, method):
-    """Hellinger and Kullback-Leibler weights; Kullback-Leibler runs 32-row
-    tiles up to radius 11 and 16-row tiles at 15, both cut by 37 rows."""
+    """Hellinger, Kullback-Leibler and Renyi weights; Kullback-Leibler runs
+    32-row tiles up to radius 11 and 16-row tiles at 15, both cut by 37 rows."""
     lib = zlib.load()
     H, W = 37, 45
     n = H * W
     z = _packed(n, n + 3)
     out = Out(n, planes=9)
-    assert lib.nlm_stochastic(z.data_ptr(), H, W, n + 3, radius, 16.0, 0.5, dist, method,
+    assert lib.nlm_stochastic(z.data_ptr(), H, W, n + 3, radius, 16.0, 0.5, dist, 0.7, method,
                               out.ptr, _stream()) == 0
     out.check(f"nlm_stochastic radius {radius} distance {dist} method {method}")
 

@@ -159,7 +159,7 @@ def test_full_size_sampled(zlib, orc, method):
 # ---------------------------------------------------------------------------
 # nlm_stochastic: Hellinger and Kullback-Leibler weights
 # ---------------------------------------------------------------------------
-BHATTACHARYYA, HELLINGER, KULLBACK_LEIBLER = 0, 1, 2
+BHATTACHARYYA, HELLINGER, KULLBACK_LEIBLER, RENYI = 0, 1, 2, 3
 
 
 def inv3_with_magnitudes(Z):
@@ -184,7 +184,15 @@ def inv3_with_magnitudes(Z):
     return cof / det, S, det, E
 
 
-def stochastic_bound(z, H, W, radius, L, h, dist, ref):
+def _expansion_magnitude(m):
+    """The cofactor expansion of det over packed entries taken in magnitude
+    (packed [9, ...] of nonnegative entry magnitudes; complex entries as
+    |Re| + |Im|)."""
+    a, ab, ac, d, ae, f = m[0], m[1] + m[2], m[3] + m[4], m[5], m[6] + m[7], m[8]
+    return a * (d * f + ae * ae) + ab * (ac * ae + ab * f) + ac * (ab * ae + ac * d)
+
+
+def stochastic_bound(z, H, W, radius, L, h, dist, ref, order=0.5):
     """[9, H*W] first-order error bound of the FP32 filter with weights
     w_ij = exp(-d_ij / h).  A relative error delta_ij of w_ij moves
     Z'_i = sum_j w_ij Z_j / sum_j w_ij by at most
@@ -200,7 +208,14 @@ def stochastic_bound(z, H, W, radius, L, h, dist, ref):
                       (error <= sum c_k |dI_k| |Z_k| + gamma_9 sum c_k |I_k| |Z_k|,
                       c_k = 2 off the diagonal), t rounded once more:
                       e <= (dtr1 + dtr2 + u |tr1 + tr2|) / 2 + u |t|,
-                      delta = (L/h)(e + 2u t) + 2^-22.
+                      delta = (L/h)(e + 2u t) + 2^-22;
+      Renyi (order b) M1 = (1-b) Z_i + b Z_j, M2 = b Z_i + (1-b) Z_j, each entry
+                      within 3u of its magnitude m (1 - b, the product and the
+                      FMA rounded), so det M_k errs by <= gamma_16 E(M_k)
+                      + 9u E(m_k) (E: the expansion in magnitudes);
+                      e = (e1 + e2)/2 + 4u (|log2 D1 + log2 D2|/2 + |h_i| + |h_j|),
+                      e_k = that / (D_k ln2) + 2^-21, delta = p ln2 (e + u t) + 2^-22
+                      with p = L / ((1-b) h).
     The test bound is 1.25 times the total."""
     Z = np.asarray(z, dtype=np.float64).reshape(9, H, W)
     R = np.asarray(ref, dtype=np.float64).reshape(9, H, W)
@@ -221,7 +236,26 @@ def stochastic_bound(z, H, W, radius, L, h, dist, ref):
             yj = slice(max(0, dy), min(H, H + dy))
             xj = slice(max(0, dx), min(W, W + dx))
             zi, zj = Z[:, ys, xs], Z[:, yj, xj]
-            if dist == KULLBACK_LEIBLER:
+            if dist == RENYI:
+                b, b1 = order, 1 - order
+                pr = L / (b1 * h)
+                t = -(0.5 * (ldz[ys, xs] + ldz[yj, xj])) / np.log(2)
+                ek = 0.0
+                lsum = 0.0
+                for (ca, cb) in ((b1, b), (b, b1)):
+                    M = ca * zi + cb * zj
+                    D = det3(M)
+                    mag_m = ca * np.abs(zi) + cb * np.abs(zj)
+                    ek = ek + 0.5 * ((gamma(16) * _expansion_magnitude(np.abs(M))
+                                      + 9 * U * _expansion_magnitude(mag_m)) / (D * np.log(2))
+                                     + 2.0 ** -21)
+                    lsum = lsum + np.log2(D)
+                    t = t + 0.5 * np.log2(D)
+                e = ek + 4 * U * (np.abs(lsum) / 2 + hz[ys, xs] + hz[yj, xj])
+                t = np.maximum(t, 0)
+                delta = pr * np.log(2) * (e + U * t) + 2.0 ** -22
+                d = pr * h * np.log(2) * t
+            elif dist == KULLBACK_LEIBLER:
                 Ii, Ij = I[:, ys, xs], I[:, yj, xj]
                 tr1 = (ck * Ii * zj).sum(axis=0)
                 tr2 = (ck * Ij * zi).sum(axis=0)
@@ -257,6 +291,23 @@ def stochastic_bound(z, H, W, radius, L, h, dist, ref):
     return 1.25 * b.reshape(9, -1)
 
 
+def test_renyi_order_one_half_is_bhattacharyya_with_half_h(zlib, orc):
+    """d_R(1/2) = 2 d_B, so Renyi of order 1/2 with h is the Bhattacharyya
+    filter with h/2: the two kernels (two pair determinants vs one) agree
+    within both bounds."""
+    H, W = 37, 70
+    w = S.scaled(S.WORKLOADS["scale_16k"], H, W)
+    z_np = w.packed_z()
+    z = torch.from_numpy(z_np).cuda().reshape(9, H, W)
+    a = zlib.nlm_stochastic(z, 3, 16.0, 2.0, RENYI, 0, order=0.5)
+    b = zlib.nlm_wishart(z, 3, 16.0, 1.0, 0)
+    torch.cuda.synchronize()
+    ref = orc.nlm_stochastic(z_np, H, W, 3, 16.0, 1.0, BHATTACHARYYA)
+    bound = (stochastic_bound(z_np, H, W, 3, 16.0, 2.0, RENYI, ref, 0.5)
+             + stochastic_bound(z_np, H, W, 3, 16.0, 1.0, BHATTACHARYYA, ref))
+    check(a.reshape(9, -1).cpu().numpy(), b.reshape(9, -1).cpu().double().numpy(), bound)
+
+
 def test_bhattacharyya_is_the_log_det_filter(zlib):
     """nlm_stochastic with the Bhattacharyya distance runs nlm_wishart's kernel."""
     H, W = 40, 75
@@ -271,7 +322,8 @@ def test_bhattacharyya_is_the_log_det_filter(zlib):
 
 @pytest.mark.parametrize("radius", [1, 3, 11])
 @pytest.mark.parametrize("dist,method,h", [(HELLINGER, 0, 0.25), (HELLINGER, 1, 0.25),
-                                           (KULLBACK_LEIBLER, 0, 4.0)])
+                                           (KULLBACK_LEIBLER, 0, 4.0), (RENYI, 0, 2.0),
+                                           (RENYI, 1, 2.0)])
 def test_stochastic_vs_oracle(zlib, orc, radius, dist, method, h):
     """Every output pixel of a ragged 37 x 70 image (two partial tiles in x, a
     ragged row pair) against the FP64 oracle under the derived bound.  The
@@ -281,14 +333,14 @@ def test_stochastic_vs_oracle(zlib, orc, radius, dist, method, h):
     w = S.scaled(S.WORKLOADS["scale_16k"], H, W)
     z_np = w.packed_z()
     z = torch.from_numpy(z_np).cuda().reshape(9, H, W)
-    out = zlib.nlm_stochastic(z, radius, 16.0, h, dist, method)
+    out = zlib.nlm_stochastic(z, radius, 16.0, h, dist, method, order=0.7)
     torch.cuda.synchronize()
-    ref = orc.nlm_stochastic(z_np, H, W, radius, 16.0, h, dist)
+    ref = orc.nlm_stochastic(z_np, H, W, radius, 16.0, h, dist, 0.7)
     check(out.reshape(9, -1).cpu().numpy(), ref,
-          stochastic_bound(z_np, H, W, radius, 16.0, h, dist, ref))
+          stochastic_bound(z_np, H, W, radius, 16.0, h, dist, ref, 0.7))
 
 
-@pytest.mark.parametrize("dist,h", [(HELLINGER, 0.25), (KULLBACK_LEIBLER, 4.0)])
+@pytest.mark.parametrize("dist,h", [(HELLINGER, 0.25), (KULLBACK_LEIBLER, 4.0), (RENYI, 2.0)])
 def test_stochastic_full_size_sampled(zlib, orc, dist, h):
     """The benchmark's 1024 x 1024 image, radius 11, in its launch
     configuration: corner, edge and interior pixels against the oracle run on a
@@ -297,7 +349,7 @@ def test_stochastic_full_size_sampled(zlib, orc, dist, h):
     R, N = 11, 1024
     w = S.scaled(S.WORKLOADS["scale_16k"], N, N)
     z = G.packed_z(w)
-    out = zlib.nlm_stochastic(z, R, 16.0, h, dist, 0).reshape(9, N, N)
+    out = zlib.nlm_stochastic(z, R, 16.0, h, dist, 0, order=0.7).reshape(9, N, N)
     torch.cuda.synchronize()
     rng = np.random.default_rng(29)
     pts = [(0, 0), (0, N - 1), (N - 1, 0), (N - 1, N - 1), (11, 511), (1012, 3)]
@@ -307,18 +359,18 @@ def test_stochastic_full_size_sampled(zlib, orc, dist, h):
         yy, xx = np.meshgrid(np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
         crop = w.packed_z((yy * N + xx).ravel().astype(np.uint64))
         ch, cw = y1 - y0, x1 - x0
-        ref_all = orc.nlm_stochastic(crop, ch, cw, R, 16.0, h, dist)
+        ref_all = orc.nlm_stochastic(crop, ch, cw, R, 16.0, h, dist, 0.7)
         k = (y - y0) * cw + (x - x0)
-        bound = stochastic_bound(crop, ch, cw, R, 16.0, h, dist, ref_all)[:, k]
+        bound = stochastic_bound(crop, ch, cw, R, 16.0, h, dist, ref_all, 0.7)[:, k]
         check(out[:, y, x].cpu().numpy(), ref_all[:, k], bound, f"pixel {(y, x)}: ")
 
 
-@pytest.mark.parametrize("dist", [HELLINGER, KULLBACK_LEIBLER])
+@pytest.mark.parametrize("dist", [HELLINGER, KULLBACK_LEIBLER, RENYI])
 def test_stochastic_constant_image_is_fixed_point(zlib, dist):
     w = S.scaled(S.WORKLOADS["plain_256"], 1, 1)
     z1 = torch.from_numpy(w.packed_z()).cuda()
     z = z1.reshape(9, 1, 1).expand(9, 20, 30).contiguous()
-    out = zlib.nlm_stochastic(z, 5, 4.0, 0.5, dist, 0)
+    out = zlib.nlm_stochastic(z, 5, 4.0, 0.5, dist, 0, order=0.7)
     torch.cuda.synchronize()
     # equal weights up to rounding of d near 0: the output is a weighted mean
     # of one value, within 2 gamma_123 of it
@@ -327,6 +379,9 @@ def test_stochastic_constant_image_is_fixed_point(zlib, dist):
 
 def test_stochastic_bad_arguments(zlib):
     z = torch.zeros((9, 8, 8), device="cuda")
-    for dist, method in ((3, 0), (-1, 0), (KULLBACK_LEIBLER, 1), (HELLINGER, 2)):
+    for dist, method in ((4, 0), (-1, 0), (KULLBACK_LEIBLER, 1), (HELLINGER, 2)):
         with pytest.raises(RuntimeError):
             zlib.nlm_stochastic(z, 3, 4.0, 1.0, dist, method)
+    for order in (0.0, 1.0, -0.5, float("inf")):
+        with pytest.raises(RuntimeError):
+            zlib.nlm_stochastic(z, 3, 4.0, 1.0, RENYI, 0, order=order)
