@@ -679,6 +679,22 @@ def main():
                              "frac_alu": tf / alu_peak,
                              "gbs": 48 * ww.n / (t * 1e-3) / 1e9}
         wishart["alu_peak_tflops"] = alu_peak
+        # saved window covariances: the forward also writes both dates' Z
+        # (72 B/pixel); the backward forms M point-wise and only correlates
+        zs = torch.empty((18, ww.H, ww.W), dtype=torch.float32, device="cuda")
+        wsb = torch.empty(zp.wishart_bwd_saved_workspace_bytes(ww.H, ww.W, 7), dtype=torch.uint8,
+                          device="cuda")
+        t_fs = timed(lambda: zp.wishart_stat_fwd_save(s1, s2, wts, 7, z_saved=zs, ws=ws_buf), sub,
+                     args.warmup, world)
+        t_bs = timed(lambda: zp.wishart_stat_bwd_saved(s1, s2, zs, 7, g1, ws=wsb), sub,
+                     args.warmup, world)
+        tf_corr = 2 * 2 * 49 * 9 * ww.n / (t_bs * 1e-3) / 1e12  # the correlation's FMAs
+        wishart["saved_z"] = {"forward_ms": t_fs, "backward_ms": t_bs,
+                              "fwd_plus_bwd_ms": t_fs + t_bs,
+                              "recompute_fwd_plus_bwd_ms": t_f + t_b,
+                              "saved_bytes": 72 * ww.n,
+                              "backward_tflops": tf_corr, "backward_frac_alu": tf_corr / alu_peak}
+        del zs, wsb
         if ww.H == 4096:
             cpu_inputs["wishart_pair_4k"] = (s1, s2)
         del ws_buf

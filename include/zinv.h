@@ -269,6 +269,41 @@ int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int64_t W, int
                      float* grad_weights, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * The change statistic with saved window covariances: the autograd trade of
+ * memory for recomputation.  wishart_stat_fwd_save is wishart_stat_fwd that
+ * also writes both dates' Z (the forward's window sums, from registers) to
+ * z_saved; wishart_stat_bwd_saved takes them instead of recomputing the window
+ * sums: a point-wise kernel forms M_t = Z_t^-1 - 2 (Z1 + Z2)^-1 of every pixel
+ * (HBM-bound), then a correlation kernel adds the weight gradient.  Same
+ * arithmetic and order as wishart_stat_bwd: the same bits.
+ *
+ *   z_saved   [18][H*W] device floats (72 bytes per pixel,
+ *             wishart_saved_bytes(H, W)): date 1's nine packed planes, then
+ *             date 2's, plane stride H*W, 4-byte aligned (16-byte aligned with
+ *             W % 4 == 0 takes 128-bit stores).  Written by the forward, read
+ *             by the backward (not modified), owned by the caller; valid for a
+ *             backward with the same s1, s2, H, W, win and weights.
+ *   ws, ws_bytes  wishart_stat_fwd_save: as wishart_stat_fwd.
+ *             wishart_stat_bwd_saved: at least
+ *             wishart_bwd_saved_workspace_bytes(H, W, win) bytes, 8-byte
+ *             aligned (per-tile partials, then the packed M of every pixel).
+ *   other arguments as wishart_stat_fwd / wishart_stat_bwd (the backward
+ *   takes no weights: they entered through Z).
+ * Images of more than 2^56 pixels are refused (ZINV_ERR_ARG), as are the
+ * argument errors of the recomputing calls; the size queries return 0 there.
+ */
+size_t wishart_saved_bytes(int64_t H, int64_t W);
+size_t wishart_bwd_saved_workspace_bytes(int64_t H, int64_t W, int win);
+int wishart_stat_fwd_save(const float* s1, const float* s2, int64_t H, int64_t W,
+                          int64_t plane_ld, int win, const float* weights, float* q_map,
+                          double* d_loss, float* z_saved, void* ws, size_t ws_bytes,
+                          void* stream);
+int wishart_stat_bwd_saved(const float* s1, const float* s2, int64_t H, int64_t W,
+                           int64_t plane_ld, int win, const float* z_saved,
+                           const double* d_grad_loss, float* grad_weights, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/*
  * wishart_stat_fwd_noalloc -- wishart_stat_fwd for callers that cannot pass a
  * device workspace: code running inside a host application or framework that
  * owns every device allocation (so cudaMalloc is unavailable or would fragment

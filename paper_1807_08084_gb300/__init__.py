@@ -85,6 +85,16 @@ def _declare_extra(lib):
     lib.nlm_stochastic.restype = ctypes.c_int
     lib.wishart_workspace_bytes.argtypes = [_I64, _I64, ctypes.c_int]
     lib.wishart_workspace_bytes.restype = ctypes.c_size_t
+    lib.wishart_saved_bytes.argtypes = [_I64, _I64]
+    lib.wishart_saved_bytes.restype = ctypes.c_size_t
+    lib.wishart_bwd_saved_workspace_bytes.argtypes = [_I64, _I64, ctypes.c_int]
+    lib.wishart_bwd_saved_workspace_bytes.restype = ctypes.c_size_t
+    lib.wishart_stat_fwd_save.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
+                                          _P, _P, ctypes.c_size_t, _P]
+    lib.wishart_stat_fwd_save.restype = ctypes.c_int
+    lib.wishart_stat_bwd_saved.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
+                                           _P, ctypes.c_size_t, _P]
+    lib.wishart_stat_bwd_saved.restype = ctypes.c_int
     lib.wishart_stat_fwd.argtypes = [_P, _P, _I64, _I64, _I64, ctypes.c_int, _P, _P, _P,
                                      _P, ctypes.c_size_t, _P]
     lib.wishart_stat_fwd.restype = ctypes.c_int
@@ -393,22 +403,84 @@ def wishart_stat_bwd(s1: torch.Tensor, s2: torch.Tensor, weights: torch.Tensor, 
     return gw
 
 
+def wishart_stat_fwd_save(s1: torch.Tensor, s2: torch.Tensor, weights: torch.Tensor,
+                          win: int = 7, want_map: bool = False,
+                          z_saved: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+    """wishart_stat_fwd that also returns both dates' window covariances Z
+    ([18, H, W] float32: date 1's packed planes, then date 2's) for
+    wishart_stat_bwd_saved: (loss, z_saved) or (loss, z_saved, q)."""
+    lib = load()
+    H, W, pld, ws = _wishart_common(s1, s2, weights, win, ws)
+    if z_saved is None:
+        z_saved = torch.empty((18, H, W), dtype=torch.float32, device=s1.device)
+    else:
+        _out(z_saved, (18, H, W), s1.device, "z_saved")
+    loss = torch.empty((), dtype=torch.float64, device=s1.device)
+    q = torch.empty((H, W), dtype=torch.float32, device=s1.device) if want_map else None
+    with torch.cuda.device(s1.device):
+        rc = lib.wishart_stat_fwd_save(_ptr(s1), _ptr(s2), H, W, pld, int(win), _ptr(weights),
+                                       _ptr(q), _ptr(loss), _ptr(z_saved), _ptr(ws), ws.numel(),
+                                       _stream(s1.device))
+    _check(rc, "wishart_stat_fwd_save")
+    return (loss, z_saved, q) if want_map else (loss, z_saved)
+
+
+def wishart_bwd_saved_workspace_bytes(H: int, W: int, win: int) -> int:
+    return int(load().wishart_bwd_saved_workspace_bytes(int(H), int(W), int(win)))
+
+
+def wishart_stat_bwd_saved(s1: torch.Tensor, s2: torch.Tensor, z_saved: torch.Tensor,
+                           win: int = 7, grad_loss: torch.Tensor | None = None,
+                           ws: torch.Tensor | None = None):
+    """g * dL/dw (float32 [win*win]) from the forward's saved Z: the same bits
+    as wishart_stat_bwd without recomputing the window sums."""
+    lib = load()
+    H, W, pld = _slc(s1, "s1")
+    if _slc(s2, "s2") != (H, W, pld) or s1.device != s2.device:
+        raise ValueError("s1 and s2 must have the same shape, plane stride and device")
+    _out(z_saved, (18, H, W), s1.device, "z_saved")
+    need = wishart_bwd_saved_workspace_bytes(H, W, win)
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=s1.device)
+    elif not ws.is_cuda or ws.dtype != torch.uint8 or ws.numel() < need:
+        raise ValueError(f"ws must be a uint8 CUDA tensor of at least {need} bytes")
+    if grad_loss is not None:
+        grad_loss = grad_loss.to(device=s1.device, dtype=torch.float64).contiguous()
+    gw = torch.empty(win * win, dtype=torch.float32, device=s1.device)
+    with torch.cuda.device(s1.device):
+        rc = lib.wishart_stat_bwd_saved(_ptr(s1), _ptr(s2), H, W, pld, int(win), _ptr(z_saved),
+                                        _ptr(grad_loss), _ptr(gw), _ptr(ws), ws.numel(),
+                                        _stream(s1.device))
+    _check(rc, "wishart_stat_bwd_saved")
+    return gw
+
+
 class WishartStat(torch.autograd.Function):
-    """loss = WishartStat.apply(s1, s2, weights, win): the change statistic with a
-    learnable window; backward recomputes Z from s1, s2 in the kernel and returns
-    the weights' gradient only (the images are data)."""
+    """loss = WishartStat.apply(s1, s2, weights, win, save_z): the change
+    statistic with a learnable window; returns the weights' gradient only (the
+    images are data).  The backward recomputes Z from s1, s2 in the kernel, or
+    with save_z=True reads the Z the forward saved (72 bytes per pixel kept
+    between the two passes)."""
 
     @staticmethod
-    def forward(ctx, s1, s2, weights, win: int = 7):
+    def forward(ctx, s1, s2, weights, win: int = 7, save_z: bool = False):
+        ctx.win, ctx.save_z = win, save_z
+        if save_z:
+            loss, z_saved = wishart_stat_fwd_save(s1, s2, weights.contiguous(), win)
+            ctx.save_for_backward(s1, s2, weights, z_saved)
+            return loss
         ctx.save_for_backward(s1, s2, weights)
-        ctx.win = win
         return wishart_stat_fwd(s1, s2, weights.contiguous(), win)
 
     @staticmethod
     def backward(ctx, g):
-        s1, s2, weights = ctx.saved_tensors
-        gw = wishart_stat_bwd(s1, s2, weights.contiguous(), ctx.win, g.reshape(()))
-        return None, None, gw.reshape(weights.shape), None
+        if ctx.save_z:
+            s1, s2, weights, z_saved = ctx.saved_tensors
+            gw = wishart_stat_bwd_saved(s1, s2, z_saved, ctx.win, g.reshape(()))
+        else:
+            s1, s2, weights = ctx.saved_tensors
+            gw = wishart_stat_bwd(s1, s2, weights.contiguous(), ctx.win, g.reshape(()))
+        return None, None, gw.reshape(weights.shape), None, None
 
 
 def zinv_det_host_workspace_bytes(chunk: int) -> int:

@@ -57,6 +57,9 @@ struct WsArgs {
   const float* weights;
   float* q_map;
   double* partial;  // [tiles][K]
+  float* z_save = nullptr;   // forward: both dates' Z, [18][H*W], or null
+  bool z_vec = false;        // z_save takes 16-byte stores (16-byte aligned, W % 4 == 0)
+  const float* m = nullptr;  // saved-Z backward: the packed M_1, M_2, [18][H*W]
 };
 
 // Loads into registers the three components of the staged pixels this thread
@@ -152,6 +155,37 @@ __device__ __forceinline__ void stage(const WsArgs& a, int t, int64_t tile, floa
   store_products<R>(v, P);
 }
 
+// Both dates' Z of the thread's 4 x 2 outputs (rows y0, y0 + 1, columns
+// x0 .. x0 + 3 of the tile) -> z_save: date 1's nine packed planes, then date
+// 2's, plane stride H*W.  Outputs outside the image are not stored.
+__device__ __forceinline__ void save_z(const WsArgs& a, int64_t ty0, int64_t tx0, int y0, int x0,
+                                       const float (&z1)[9][2][4], const float (&z2)[9][2][4]) {
+  const int64_t n = a.H * a.W, gx = tx0 + x0;
+  const bool vec = a.z_vec && gx + 4 <= a.W;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int64_t gy = ty0 + y0 + r;
+    if (gy >= a.H) continue;
+    float* base = a.z_save + gy * a.W + gx;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      if (vec) {
+        __stcs(reinterpret_cast<float4*>(base + c * n),
+               make_float4(z1[c][r][0], z1[c][r][1], z1[c][r][2], z1[c][r][3]));
+        __stcs(reinterpret_cast<float4*>(base + (9 + c) * n),
+               make_float4(z2[c][r][0], z2[c][r][1], z2[c][r][2], z2[c][r][3]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (gx + i < a.W) {
+            __stcs(base + c * n + i, z1[c][r][i]);
+            __stcs(base + (9 + c) * n + i, z2[c][r][i]);
+          }
+      }
+    }
+  }
+}
+
 // Fixed-order block reduction of one double per thread; returns the sum in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
@@ -166,7 +200,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-template <int R>
+template <int R, bool SAVE>
 __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
   using T = WTile<R>;
   extern __shared__ __align__(16) float smem[];
@@ -205,6 +239,7 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
             for (int i = 0; i < 4; ++i) z0[c][r][i] = z[c][r][i];
         continue;
       }
+      if constexpr (SAVE) save_z(a, ty0, tx0, y0, x0, z0, z);
       // Both dates' Z are in registers: the thread takes the compensated
       // log-dets of Z1, Z2 and Z1 + Z2 of its own 4 x 2 outputs, two adjacent
       // outputs per pass on packed float2 pairs, and stores and adds its q in
@@ -434,6 +469,128 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Backward from saved Z (the forward's z_save): the window sums are not
+// recomputed.  k_wishart_m turns each pixel's saved Z1, Z2 into the packed
+// gradient forms of M_t = W_t - 2 W12 (the same compensated inverses and
+// rounding as the recomputing backward); k_wishart_corr then correlates them
+// with the staged channel products.  Results are the recomputing backward's
+// bits, as both compute Z with the same tap order.
+// ---------------------------------------------------------------------------
+
+// Pixels p and p + half of `n` (half = ceil(n/2)) as the two halves of packed
+// pairs; the last thread of an odd n computes its second pixel twice and
+// stores it once.
+__global__ void __launch_bounds__(256) k_wishart_m(const float* z, float* m, int64_t n) {
+  const int64_t half = (n + 1) / 2;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < half;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = p + half < n ? p + half : p;
+    float2 z1[9], z2[9], z12[9], w1[9], w2[9], w12[9], d;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      z1[c] = make_float2(__ldcs(z + c * n + p), __ldcs(z + c * n + q));
+      z2[c] = make_float2(__ldcs(z + (9 + c) * n + p), __ldcs(z + (9 + c) * n + q));
+      z12[c] = add_rn(z1[c], z2[c]);
+    }
+    adjugate_inv_det_comp<float2>(z12, w12, d);
+    adjugate_inv_det_comp<float2>(z1, w1, d);
+    adjugate_inv_det_comp<float2>(z2, w2, d);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const float two = (c == 0 || c == 5 || c == 8) ? 1.0f : 2.0f;
+      m[c * n + p] = two * fmaf(-2.0f, w12[c].x, w1[c].x);
+      m[(9 + c) * n + p] = two * fmaf(-2.0f, w12[c].x, w2[c].x);
+      if (q != p) {
+        m[c * n + q] = two * fmaf(-2.0f, w12[c].y, w1[c].y);
+        m[(9 + c) * n + q] = two * fmaf(-2.0f, w12[c].y, w2[c].y);
+      }
+    }
+  }
+}
+
+// dL/dw_k per tile from saved M: per date (date 2 first, the recomputing
+// backward's order), the tile's products P and its M_t (zero outside the
+// image) are staged in shared memory, then the same correlation.
+template <int R>
+__global__ void __launch_bounds__(kWT, 4) k_wishart_corr(WsArgs a) {
+  using T = WTile<R>;
+  constexpr int L = T::L;
+  constexpr int K = T::K;
+  constexpr int TILE = kTH * kTW;
+  extern __shared__ __align__(16) float smem[];
+  float* P = smem;
+  float* G = smem + T::P_FLOATS;  // [9][kTH][kTW]: one date's packed M
+  static_assert(T::K * (kWT + 1) <= T::P_FLOATS, "the tap partials fit in P");
+  const int64_t n = a.H * a.W;
+  const int64_t tiles_x = (a.W + kTW - 1) / kTW;
+  const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
+  const int y0 = 2 * (threadIdx.x / kTX), x0 = 4 * (threadIdx.x % kTX);
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
+    float acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
+#pragma unroll 1
+    for (int t = 1; t >= 0; --t) {
+      __syncthreads();
+      stage<R>(a, t, tile, P);
+#pragma unroll 1
+      for (int e = threadIdx.x; e < 9 * TILE; e += kWT) {
+        const int c = e / TILE, o = e - c * TILE;
+        const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
+        G[e] = (gy < a.H && gx < a.W) ? __ldcs(a.m + (9 * t + c) * n + gy * a.W + gx) : 0.0f;
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int c = 0; c < 9; ++c) {
+        const float* Gc = G + c * TILE;
+        float g[2][4];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const float4 gv = *reinterpret_cast<const float4*>(Gc + (y0 + r) * kTW + x0);
+          g[r][0] = gv.x;
+          g[r][1] = gv.y;
+          g[r][2] = gv.z;
+          g[r][3] = gv.w;
+        }
+        const float* Pc = P + c * T::PLANE;
+#pragma unroll
+        for (int iy = 0; iy <= L; ++iy) {
+          float row[4 * T::NV];
+          load_row<R>(Pc + (y0 + iy) * T::SWP + x0, row);
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int dy = iy - r;
+            if (dy < 0 || dy >= L) continue;
+#pragma unroll
+            for (int dx = 0; dx < L; ++dx)
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                acc[dy * L + dx] = fmaf(g[r][i], row[i + dx], acc[dy * L + dx]);
+          }
+        }
+      }
+    }
+    // fixed-order tap sums over the block, as the recomputing backward
+    __syncthreads();
+    float* accs = P;
+#pragma unroll
+    for (int k = 0; k < K; ++k) accs[k * (kWT + 1) + threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += kWT) {
+      float sum = 0.0f, err = 0.0f;
+#pragma unroll 8
+      for (int t = 0; t < kWT; ++t) {
+        float e;
+        two_sum(sum, accs[k * (kWT + 1) + t], sum, e);
+        err += e;
+      }
+      a.partial[tile * K + k] = (double)sum + (double)err;
+    }
+  }
+}
+
 // out[k] = scale * sum_tiles partial[tile][k], summed in a fixed order.
 // double_out: out is double (the loss); otherwise float (the weight gradient)
 // and scale is read from *g (the upstream gradient, a device double).
@@ -466,6 +623,21 @@ size_t bwd_smem() {
   return (T::P_FLOATS + 2 * T::Z_FLOATS) * sizeof(float);
 }
 
+int64_t tile_count(int64_t H, int64_t W);
+
+template <int R>
+size_t corr_smem() {
+  using T = WTile<R>;
+  return (T::P_FLOATS + T::Z_FLOATS) * sizeof(float);
+}
+
+// Workspace of the saved-Z backward: the per-tile partials, then (256-byte
+// aligned) the packed M_1, M_2 of every pixel.
+size_t partials_bytes(int64_t H, int64_t W, int win) {
+  const size_t b = (size_t)tile_count(H, W) * (size_t)(win * win) * sizeof(double);
+  return (b + 255) / 256 * 256;
+}
+
 int64_t tile_count(int64_t H, int64_t W) {
   return ((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);
 }
@@ -483,21 +655,24 @@ int launch_tiles(Kern kernel, size_t smem, const WsArgs& a, cudaStream_t s) {
   return launch_status();
 }
 
-// Shared argument checks; fills a and tiles.  Returns ZINV_OK or an error.
+// Shared argument checks; fills a.  `weights` may be null only when
+// !need_weights; the workspace must hold `need` bytes (0: the per-tile
+// partials).  Returns ZINV_OK or an error.
 int prepare(const float* s1, const float* s2, int64_t H, int64_t W, int64_t plane_ld, int win,
-            const float* weights, void* ws, size_t ws_bytes, WsArgs& a, DeviceInfo& di) {
+            const float* weights, void* ws, size_t ws_bytes, WsArgs& a, DeviceInfo& di,
+            bool need_weights = true, size_t need = 0) {
   if (H < 1 || W < 1 || H > kMaxLd / W) return ZINV_ERR_ARG;
   if (win != 3 && win != 5 && win != 7) return ZINV_ERR_ARG;
   if (plane_ld < H * W || plane_ld > kMaxLd) return ZINV_ERR_ARG;
-  if (!s1 || !s2 || !weights || !ws) return ZINV_ERR_ARG;
+  if (!s1 || !s2 || (need_weights && !weights) || !ws) return ZINV_ERR_ARG;
   if (!aligned(s1, 8) || !aligned(s2, 8) || !aligned(weights, 4) || !aligned(ws, 8))
     return ZINV_ERR_ARG;
-  const size_t need = (size_t)tile_count(H, W) * (size_t)(win * win) * sizeof(double);
+  if (need == 0) need = (size_t)tile_count(H, W) * (size_t)(win * win) * sizeof(double);
   if (ws_bytes < need) return ZINV_ERR_ARG;
   int rc = device_info(&di);
   if (rc != ZINV_OK) return rc;
-  if (!device_accessible(s1) || !device_accessible(s2) || !device_accessible(weights) ||
-      !device_accessible(ws))
+  if (!device_accessible(s1) || !device_accessible(s2) ||
+      (weights && !device_accessible(weights)) || !device_accessible(ws))
     return ZINV_ERR_ARG;
   a.s[0] = reinterpret_cast<const float2*>(s1);
   a.s[1] = reinterpret_cast<const float2*>(s2);
@@ -531,9 +706,9 @@ extern "C" int wishart_stat_fwd(const float* s1, const float* s2, int64_t H, int
   a.q_map = q_map;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (win) {
-    case 3: rc = launch_tiles(k_wishart_fwd<1>, fwd_smem<1>(), a, st); break;
-    case 5: rc = launch_tiles(k_wishart_fwd<2>, fwd_smem<2>(), a, st); break;
-    default: rc = launch_tiles(k_wishart_fwd<3>, fwd_smem<3>(), a, st); break;
+    case 3: rc = launch_tiles(k_wishart_fwd<1, false>, fwd_smem<1>(), a, st); break;
+    case 5: rc = launch_tiles(k_wishart_fwd<2, false>, fwd_smem<2>(), a, st); break;
+    default: rc = launch_tiles(k_wishart_fwd<3, false>, fwd_smem<3>(), a, st); break;
   }
   if (rc != ZINV_OK) return rc;
   k_reduce_tiles<<<1, kRedThreads, 0, st>>>(a.partial, tile_count(H, W), 1, nullptr, d_loss, 1);
@@ -558,6 +733,87 @@ extern "C" int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int
     case 3: rc = launch_tiles(k_wishart_bwd<1>, bwd_smem<1>(), a, st); break;
     case 5: rc = launch_tiles(k_wishart_bwd<2>, bwd_smem<2>(), a, st); break;
     default: rc = launch_tiles(k_wishart_bwd<3>, bwd_smem<3>(), a, st); break;
+  }
+  if (rc != ZINV_OK) return rc;
+  k_reduce_tiles<<<win * win, kRedThreads, 0, st>>>(a.partial, tile_count(H, W), win * win,
+                                                    d_grad_loss, grad_weights, 0);
+  return launch_status();
+}
+
+namespace zinv {
+namespace {
+// Largest image of the saved-Z calls: 72 bytes per pixel stay within size_t.
+constexpr int64_t kMaxSavedPixels = (int64_t)1 << 56;
+}  // namespace
+}  // namespace zinv
+
+extern "C" size_t wishart_saved_bytes(int64_t H, int64_t W) {
+  if (H < 1 || W < 1 || H > zinv::kMaxSavedPixels / W) return 0;
+  return (size_t)18 * (size_t)(H * W) * sizeof(float);
+}
+
+extern "C" size_t wishart_bwd_saved_workspace_bytes(int64_t H, int64_t W, int win) {
+  if (H < 1 || W < 1 || win < 1 || H > zinv::kMaxSavedPixels / W) return 0;
+  return zinv::partials_bytes(H, W, win) + (size_t)18 * (size_t)(H * W) * sizeof(float);
+}
+
+extern "C" int wishart_stat_fwd_save(const float* s1, const float* s2, int64_t H, int64_t W,
+                                     int64_t plane_ld, int win, const float* weights,
+                                     float* q_map, double* d_loss, float* z_saved, void* ws,
+                                     size_t ws_bytes, void* stream) {
+  using namespace zinv;
+  WsArgs a;
+  DeviceInfo di;
+  if (!d_loss || !z_saved || !aligned(d_loss, 8) || !aligned(q_map, 4) || !aligned(z_saved, 4))
+    return ZINV_ERR_ARG;
+  if (H < 1 || W < 1 || H > kMaxSavedPixels / W) return ZINV_ERR_ARG;
+  int rc = prepare(s1, s2, H, W, plane_ld, win, weights, ws, ws_bytes, a, di);
+  if (rc != ZINV_OK) return rc;
+  if (!device_accessible(d_loss) || !device_accessible(z_saved) ||
+      (q_map && !device_accessible(q_map)))
+    return ZINV_ERR_ARG;
+  a.q_map = q_map;
+  a.z_save = z_saved;
+  a.z_vec = aligned(z_saved, 16) && (W % 4) == 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (win) {
+    case 3: rc = launch_tiles(k_wishart_fwd<1, true>, fwd_smem<1>(), a, st); break;
+    case 5: rc = launch_tiles(k_wishart_fwd<2, true>, fwd_smem<2>(), a, st); break;
+    default: rc = launch_tiles(k_wishart_fwd<3, true>, fwd_smem<3>(), a, st); break;
+  }
+  if (rc != ZINV_OK) return rc;
+  k_reduce_tiles<<<1, kRedThreads, 0, st>>>(a.partial, tile_count(H, W), 1, nullptr, d_loss, 1);
+  return launch_status();
+}
+
+extern "C" int wishart_stat_bwd_saved(const float* s1, const float* s2, int64_t H, int64_t W,
+                                      int64_t plane_ld, int win, const float* z_saved,
+                                      const double* d_grad_loss, float* grad_weights, void* ws,
+                                      size_t ws_bytes, void* stream) {
+  using namespace zinv;
+  WsArgs a;
+  DeviceInfo di;
+  if (!z_saved || !grad_weights || !aligned(z_saved, 4) || !aligned(grad_weights, 4) ||
+      !aligned(d_grad_loss, 8))
+    return ZINV_ERR_ARG;
+  if (H < 1 || W < 1 || H > kMaxSavedPixels / W || win < 1) return ZINV_ERR_ARG;
+  const size_t need = wishart_bwd_saved_workspace_bytes(H, W, win);
+  int rc = prepare(s1, s2, H, W, plane_ld, win, nullptr, ws, ws_bytes, a, di, false, need);
+  if (rc != ZINV_OK) return rc;
+  if (!device_accessible(z_saved) || !device_accessible(grad_weights) ||
+      (d_grad_loss && !device_accessible(d_grad_loss)))
+    return ZINV_ERR_ARG;
+  float* m = reinterpret_cast<float*>(static_cast<char*>(ws) + partials_bytes(H, W, win));
+  a.m = m;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = H * W;
+  k_wishart_m<<<(unsigned)cover_blocks((n + 1) / 2, 256), 256, 0, st>>>(z_saved, m, n);
+  rc = launch_status();
+  if (rc != ZINV_OK) return rc;
+  switch (win) {
+    case 3: rc = launch_tiles(k_wishart_corr<1>, corr_smem<1>(), a, st); break;
+    case 5: rc = launch_tiles(k_wishart_corr<2>, corr_smem<2>(), a, st); break;
+    default: rc = launch_tiles(k_wishart_corr<3>, corr_smem<3>(), a, st); break;
   }
   if (rc != ZINV_OK) return rc;
   k_reduce_tiles<<<win * win, kRedThreads, 0, st>>>(a.partial, tile_count(H, W), win * win,
@@ -637,9 +893,9 @@ extern "C" int wishart_stat_fwd_noalloc(const float* s1, const float* s2, int64_
   a.partial = scratch;  // every tile writes its own slot before the reduce reads it
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (win) {
-    case 3: rc = launch_tiles(k_wishart_fwd<1>, fwd_smem<1>(), a, st); break;
-    case 5: rc = launch_tiles(k_wishart_fwd<2>, fwd_smem<2>(), a, st); break;
-    default: rc = launch_tiles(k_wishart_fwd<3>, fwd_smem<3>(), a, st); break;
+    case 3: rc = launch_tiles(k_wishart_fwd<1, false>, fwd_smem<1>(), a, st); break;
+    case 5: rc = launch_tiles(k_wishart_fwd<2, false>, fwd_smem<2>(), a, st); break;
+    default: rc = launch_tiles(k_wishart_fwd<3, false>, fwd_smem<3>(), a, st); break;
   }
   if (rc != ZINV_OK) return rc;
   k_reduce_tiles<<<1, kRedThreads, 0, st>>>(a.partial, tiles, 1, nullptr, d_loss, 1);

@@ -93,6 +93,23 @@ def test_host_argument_checks():
     for dist, method in ((0, 0), (1, 1), (2, 0), (3, 1)):
         assert lib.nlm_stochastic(z9, 10, 10, 100, 3, 4.0, 1.0, dist, 0.5, method, z9,
                                   None) == -3
+    # saved window covariances of the Wishart statistic
+    assert lib.wishart_saved_bytes(0, 5) == 0 and lib.wishart_saved_bytes(1 << 30, 1 << 30) == 0
+    assert lib.wishart_saved_bytes(4, 8) == 18 * 32 * 4
+    need = lib.wishart_bwd_saved_workspace_bytes(40, 70, 7)
+    assert need >= lib.wishart_workspace_bytes(40, 70, 7) + 72 * 40 * 70 and need % 8 == 0
+    f = P(fake)
+    assert lib.wishart_stat_fwd_save(f, f, 40, 70, 2800, 7, f, None, f, None, f, 1 << 30,
+                                     None) == -1                      # no z_saved
+    assert lib.wishart_stat_fwd_save(f, f, 40, 70, 2800, 7, f, None, f, f, f, 1 << 30,
+                                      None) == -3
+    assert lib.wishart_stat_bwd_saved(f, f, 40, 70, 2800, 7, f, None, f, f, need - 8,
+                                      None) == -1                     # workspace too small
+    assert lib.wishart_stat_bwd_saved(f, f, 40, 70, 2800, 7, None, None, f, f, need,
+                                      None) == -1                     # no z_saved
+    assert lib.wishart_stat_bwd_saved(f, f, 40, 70, 2800, 6, f, None, f, f, need,
+                                      None) == -1                     # window
+    assert lib.wishart_stat_bwd_saved(f, f, 40, 70, 2800, 7, f, None, f, f, need, None) == -3
     assert lib.zinv_det_host_workspace_bytes(0) == 0
     assert lib.zinv_det_host_workspace_bytes(1024) >= 3 * 40 * 1024
 

@@ -193,6 +193,22 @@ def test_wishart_outputs_and_workspace(zlib, shape, win):
                                 g.data_ptr(), grad.ptr, ws.ptr, ws_bytes, _stream()) == 0
     grad.check("grad_weights")
     ws.check("workspace (backward)", written=False)
+    # saved window covariances: the forward writes exactly the 18 planes of
+    # z_saved; the backward reads them and keeps to its larger workspace
+    zs = Out(n, planes=18)
+    assert lib.wishart_stat_fwd_save(s1.data_ptr(), s2.data_ptr(), H, W, n, win, wts.data_ptr(),
+                                     q.ptr, loss.ptr, zs.ptr, ws.ptr, ws_bytes, _stream()) == 0
+    zs.check("z_saved")
+    ws.check("workspace (forward, saving)", written=False)
+    wsb_bytes = lib.wishart_bwd_saved_workspace_bytes(H, W, win)
+    assert wsb_bytes % 8 == 0 and wsb_bytes >= ws_bytes + 72 * n
+    wsb = Out(wsb_bytes // 8, "f64")
+    grad2 = Out(win * win)
+    assert lib.wishart_stat_bwd_saved(s1.data_ptr(), s2.data_ptr(), H, W, n, win, zs.ptr,
+                                      g.data_ptr(), grad2.ptr, wsb.ptr, wsb_bytes, _stream()) == 0
+    grad2.check("grad_weights (saved Z)")
+    wsb.check("workspace (backward, saved Z)", written=False)
+    zs.check("z_saved after the backward")
 
 
 @pytest.mark.parametrize("staged", [False, True])

@@ -206,3 +206,73 @@ def test_full_size_gradient_and_loss_vs_oracle(zlib, tmp_path):
     assert err <= G_REL, f"grad rel err {err:.3e}"
     # the loss within 2e-4 per pixel (the per-pixel bound is typically 1e-5..1e-4)
     assert abs(float(loss) - ref_loss) <= 2e-4 * w.H * w.W, (float(loss), ref_loss)
+
+
+# ---------------------------------------------------------------------------
+# saved window covariances (wishart_stat_fwd_save / wishart_stat_bwd_saved)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("win", [3, 5, 7])
+@pytest.mark.parametrize("shape", [(70, 100), (37, 45)])  # 128-bit and 32-bit Z stores
+def test_saved_z_matches_recompute_and_oracle(zlib, orc, win, shape):
+    """The saved path gives the recomputing path's bits (loss, q map, weight
+    gradient), and the saved Z is each date's window covariance: against the
+    oracle within gamma_(K+3) sqrt(Z_ii Z_jj) per entry (K positive-weight
+    terms of FP32 products; off-diagonal sums are bounded by Cauchy-Schwarz)."""
+    H, W = shape
+    _, c1, c2 = pair(H, W)
+    s1, s2 = torch.from_numpy(c1).cuda(), torch.from_numpy(c2).cuda()
+    wts = weights(win, 3)
+    wd = torch.from_numpy(wts).cuda()
+    loss, q = zlib.wishart_stat_fwd(s1, s2, wd, win, want_map=True)
+    loss2, zs, q2 = zlib.wishart_stat_fwd_save(s1, s2, wd, win, want_map=True)
+    g = torch.tensor(-0.75, dtype=torch.float64, device="cuda")
+    gw = zlib.wishart_stat_bwd(s1, s2, wd, win, g)
+    gw2 = zlib.wishart_stat_bwd_saved(s1, s2, zs, win, g)
+    torch.cuda.synchronize()
+    assert float(loss) == float(loss2) and torch.equal(q, q2)
+    assert torch.equal(gw, gw2)
+    K = win * win
+    for t, c in ((0, c1), (1, c2)):
+        ref = orc.multilook(c, win, wts)
+        got = zs[9 * t:9 * t + 9].reshape(9, -1).cpu().double().numpy()
+        dg = ref[[0, 5, 8]]
+        scale = np.sqrt(np.stack([dg[0], dg[0] * dg[1], dg[0] * dg[1], dg[0] * dg[2],
+                                  dg[0] * dg[2], dg[1], dg[1] * dg[2], dg[1] * dg[2], dg[2]]))
+        scale[[0, 5, 8]] = dg
+        assert np.all(np.abs(got - ref) <= gamma(K + 3) * scale)
+
+
+def test_saved_z_full_size_and_autograd(zlib):
+    """The 4096 x 4096 pair in the benchmark's configuration: the saved path's
+    loss and gradient are the recomputing path's bits, and WishartStat with
+    save_z gives the same gradient through autograd."""
+    from paper_1807_08084_gb300.synth import gpu as G
+    w = S.WORKLOADS["wishart_pair_4k"]
+    s1, s2 = G.image(w, 0), G.image(w, 1)
+    wd = torch.full((49,), 1 / 49, device="cuda")
+    loss = zlib.wishart_stat_fwd(s1, s2, wd, 7)
+    g = zlib.wishart_stat_bwd(s1, s2, wd, 7)
+    loss2, zs = zlib.wishart_stat_fwd_save(s1, s2, wd, 7)
+    g2 = zlib.wishart_stat_bwd_saved(s1, s2, zs, 7)
+    torch.cuda.synchronize()
+    assert float(loss) == float(loss2) and torch.equal(g, g2)
+    del zs
+    wv = wd.clone().requires_grad_(True)
+    zlib.WishartStat.apply(s1, s2, wv, 7, True).backward()
+    torch.cuda.synchronize()
+    assert torch.equal(wv.grad, g)
+
+
+def test_saved_z_bad_arguments(zlib):
+    H, W = 16, 32
+    _, c1, c2 = pair(H, W)
+    s1, s2 = torch.from_numpy(c1).cuda(), torch.from_numpy(c2).cuda()
+    wd = torch.from_numpy(weights(3)).cuda()
+    with pytest.raises(ValueError):
+        zlib.wishart_stat_fwd_save(s1, s2, wd, 3, z_saved=torch.empty((9, H, W), device="cuda"))
+    _, zs = zlib.wishart_stat_fwd_save(s1, s2, wd, 3)
+    with pytest.raises(ValueError):
+        zlib.wishart_stat_bwd_saved(s1, s2, zs[:9], 3)
+    with pytest.raises(ValueError):
+        zlib.wishart_stat_bwd_saved(s1, s2, zs, 3, ws=torch.empty(8, dtype=torch.uint8,
+                                                                  device="cuda"))
