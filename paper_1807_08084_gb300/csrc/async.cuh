@@ -15,6 +15,14 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) 
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
+// 4-byte copy through L1; with valid == false nothing is read and the shared
+// word is zeroed (source size 0; gmem_src must still be a valid address).
+__device__ __forceinline__ void cp_async4_zfill(void* smem_dst, const void* gmem_src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gmem_src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
 // Closes the group of copies issued so far by this thread.
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");

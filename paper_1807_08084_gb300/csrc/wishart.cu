@@ -534,13 +534,18 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_corr(WsArgs a) {
 #pragma unroll 1
     for (int t = 1; t >= 0; --t) {
       __syncthreads();
-      stage<R>(a, t, tile, P);
-#pragma unroll 1
+      // M_t of the tile (zero outside the image) copied asynchronously while
+      // the products are staged
+#pragma unroll 8
       for (int e = threadIdx.x; e < 9 * TILE; e += kWT) {
         const int c = e / TILE, o = e - c * TILE;
         const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
-        G[e] = (gy < a.H && gx < a.W) ? __ldcs(a.m + (9 * t + c) * n + gy * a.W + gx) : 0.0f;
+        const bool in = gy < a.H && gx < a.W;
+        cp_async4_zfill(G + e, in ? a.m + (9 * t + c) * n + gy * a.W + gx : a.m, in);
       }
+      cp_async_commit();
+      stage<R>(a, t, tile, P);
+      cp_async_wait<0>();
       __syncthreads();
 #pragma unroll 1
       for (int c = 0; c < 9; ++c) {
