@@ -200,8 +200,10 @@ def stochastic_bound(z, H, W, radius, L, h, dist, ref, order=0.5):
     (the exact weights from the FP64 distances), plus the FP32 rounding of the
     two weighted sums, 2 gamma_(n_i + 2) max_j |Z_jc|.  Per pair:
       Bhattacharyya   delta = (L/h) ln2 e + 2^-22, e the error of t as for nlm_wishart;
-      Hellinger       w = 2^(-(log2 e / h)(1 - x)), x = 2^(-L t) <= 1:
-                      delta = (L ln2 e + d_B u + 2^-22 + 3u) / h + 2^-22;
+      Hellinger       w = 2^(-(log2 e / h)(1 - x)), x = 2^(-L t) <= 1; over the
+                      interval t +- e the derivative of x is at most
+                      L ln2 x_m, x_m = min(1, x 2^(L e)), so
+                      delta = min(1, x_m (L ln2 e + d_B u + 2^-22) + 3u) / h + 2^-22;
       Kullback-Leibler  t = (tr(I_i Z_j) + tr(I_j Z_i)) / 2 - 3 with I the
                       compensated inverse, |dI_k| <= 6u |I_k| + 2 gamma_3^2 (S_k + E |I_k|) / det
                       (Dot2 cofactors and det), each trace a 9-term FP32 FMA chain
@@ -277,7 +279,9 @@ def stochastic_bound(z, H, W, radius, L, h, dist, ref, order=0.5):
                      + 4 * U * (np.abs(np.log2(det)) + 3 + hz[ys, xs] + hz[yj, xj]))
                 dB = L * np.maximum(np.log(det / 8) - 0.5 * (ldz[ys, xs] + ldz[yj, xj]), 0)
                 if dist == HELLINGER:
-                    delta = (L * np.log(2) * e + dB * U + 2.0 ** -22 + 3 * U) / h + 2.0 ** -22
+                    xm = np.minimum(1.0, np.exp(-dB) * 2.0 ** np.minimum(L * e, 60.0))
+                    dh = np.minimum(1.0, xm * (L * np.log(2) * e + dB * U + 2.0 ** -22) + 3 * U)
+                    delta = dh / h + 2.0 ** -22
                     d = 1 - np.exp(-dB)
                 else:
                     delta = (L / h) * np.log(2) * e + 2.0 ** -22
@@ -385,3 +389,46 @@ def test_stochastic_bad_arguments(zlib):
     for order in (0.0, 1.0, -0.5, float("inf")):
         with pytest.raises(RuntimeError):
             zlib.nlm_stochastic(z, 3, 4.0, 1.0, RENYI, 0, order=order)
+
+
+def ill_conditioned_image(H, W, cond=1e3, looks=16, seed=31):
+    """[9, H*W] FP32 sample covariances of `looks` looks of one Sigma =
+    U diag(1, cond^-1/2, 1/cond) U^H (U a seeded Haar matrix): neighbours are
+    close in the Wishart sense, every pixel is ill-conditioned."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+    Q, R = np.linalg.qr(G)
+    Q = Q * (np.diag(R) / np.abs(np.diag(R)))
+    Sig = (Q * np.array([1.0, cond ** -0.5, 1.0 / cond])) @ Q.conj().T
+    C = np.linalg.cholesky(Sig)
+    g = (rng.standard_normal((H * W, looks, 3)) + 1j * rng.standard_normal((H * W, looks, 3))) / np.sqrt(2)
+    s = g @ C.T
+    Z = np.einsum("nli,nlj->nij", s, s.conj()) / looks
+    return np.stack([Z[:, 0, 0].real, Z[:, 0, 1].real, Z[:, 0, 1].imag, Z[:, 0, 2].real,
+                     Z[:, 0, 2].imag, Z[:, 1, 1].real, Z[:, 1, 2].real, Z[:, 1, 2].imag,
+                     Z[:, 2, 2].real]).astype(np.float32)
+
+
+@pytest.mark.parametrize("dist,method,h,order", [(BHATTACHARYYA, 0, 1.0, 0.5),
+                                                 (BHATTACHARYYA, 1, 1.0, 0.5),
+                                                 (HELLINGER, 0, 0.25, 0.5),
+                                                 (KULLBACK_LEIBLER, 0, 4.0, 0.5),
+                                                 (RENYI, 0, 2.0, 0.1), (RENYI, 1, 2.0, 0.1),
+                                                 (RENYI, 0, 8.0, 0.95)])
+def test_stochastic_ill_conditioned_vs_oracle(zlib, orc, dist, method, h, order):
+    """Every pixel of a 24 x 40 image of 16-look covariances of one Sigma with
+    cond 1e3 against the oracle under the derived bounds (the determinants'
+    and traces' cond-dependent terms are the ones exercised), for every
+    distance and Renyi orders near 0 and 1.  From cond ~1e4 the bounds of the
+    determinant-based distances exceed the data's scale: rounding the FP32
+    pair sum alone moves det(Z_i + Z_j) by up to u E / D relative."""
+    H, W = 24, 40
+    z_np = ill_conditioned_image(H, W)
+    z = torch.from_numpy(z_np).cuda().reshape(9, H, W)
+    out = zlib.nlm_stochastic(z, 3, 16.0, h, dist, method, order=order)
+    torch.cuda.synchronize()
+    ref = orc.nlm_stochastic(z_np, H, W, 3, 16.0, h, dist, order)
+    assert np.median(np.abs(ref - z_np).max(axis=0) / np.abs(ref).max(axis=0)) > 1e-3  # it filters
+    check(out.reshape(9, -1).cpu().numpy(), ref,
+          stochastic_bound(z_np, H, W, 3, 16.0, h, dist, ref, order))
+
