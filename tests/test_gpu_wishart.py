@@ -276,3 +276,38 @@ def test_saved_z_bad_arguments(zlib):
     with pytest.raises(ValueError):
         zlib.wishart_stat_bwd_saved(s1, s2, zs, 3, ws=torch.empty(8, dtype=torch.uint8,
                                                                   device="cuda"))
+
+
+@pytest.mark.parametrize("pad", [5, 6])  # plane stride H*W + pad (odd / even)
+def test_padded_planes_give_the_same_bits(zlib, pad):
+    """Single-look images whose three planes sit H*W + pad elements apart give
+    the bits of the unpadded images: the Wishart statistic and gradient (both
+    paths) and the boxcar and weighted multilook (an odd pad takes the
+    boxcar's 8-byte copies, an even one its 16-byte copies)."""
+    H, W = 37, 70
+    _, c1, c2 = pair(H, W)
+    s1, s2 = torch.from_numpy(c1).cuda(), torch.from_numpy(c2).cuda()
+
+    def padded(s):
+        buf = torch.zeros(3 * (H * W + pad), dtype=torch.complex64, device="cuda")
+        v = buf.as_strided((3, H, W), (H * W + pad, W, 1))
+        v.copy_(s)
+        return v
+
+    p1, p2 = padded(s1), padded(s2)
+    wd = torch.from_numpy(weights(7, 1)).cuda()
+    loss, q = zlib.wishart_stat_fwd(s1, s2, wd, 7, want_map=True)
+    lossp, qp = zlib.wishart_stat_fwd(p1, p2, wd, 7, want_map=True)
+    g, gp = zlib.wishart_stat_bwd(s1, s2, wd, 7), zlib.wishart_stat_bwd(p1, p2, wd, 7)
+    _, zs = zlib.wishart_stat_fwd_save(s1, s2, wd, 7)
+    _, zsp = zlib.wishart_stat_fwd_save(p1, p2, wd, 7)
+    gs = zlib.wishart_stat_bwd_saved(p1, p2, zsp, 7)
+    zi, dt = zlib.multilook_zinv_det(s1, 7)
+    zip_, dtp = zlib.multilook_zinv_det(p1, 7)
+    wzi, wdt = zlib.multilook_zinv_det(s1, 5, torch.from_numpy(weights(5, 2)).cuda())
+    wzip, wdtp = zlib.multilook_zinv_det(p1, 5, torch.from_numpy(weights(5, 2)).cuda())
+    torch.cuda.synchronize()
+    assert float(loss) == float(lossp) and torch.equal(q, qp)
+    assert torch.equal(g, gp) and torch.equal(g, gs) and torch.equal(zs, zsp)
+    assert torch.equal(zi, zip_) and torch.equal(dt, dtp)
+    assert torch.equal(wzi, wzip) and torch.equal(wdt, wdtp)
