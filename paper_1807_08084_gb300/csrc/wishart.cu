@@ -384,6 +384,15 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
   // again (its correlation).  Staging loads directly (no register prefetch:
   // the registers go to the 49 tap accumulators; the other CTAs on the SM
   // cover the load latency).
+  // 3 x 3 and 5 x 5: each stage's single-look data is loaded into registers
+  // during the previous phase (1.36 -> 1.30 and 1.80 -> 1.68 ms on the 4096^2
+  // pair); the 7 x 7 kernel, whose 49 taps and 49 accumulators fill the
+  // registers, spilled that way (2.70 -> 3.21 ms) and loads each stage directly.
+  constexpr bool PREFETCH = R < 3;
+  float2 v[PREFETCH ? T::KO : 1][3];
+  if constexpr (PREFETCH) {
+    if ((int64_t)blockIdx.x < tiles) prefetch<R>(a, 0, blockIdx.x, v);
+  }
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
     float acc[K];
@@ -393,7 +402,18 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
     for (int phase = 0; phase < 3; ++phase) {
       const int t = phase == 1 ? 1 : 0;  // the date staged now
       __syncthreads();
-      stage<R>(a, t, tile, P);
+      if constexpr (PREFETCH) {
+        store_products<R>(v, P);
+        if (phase == 0) {
+          prefetch<R>(a, 1, tile, v);
+        } else if (phase == 1) {
+          prefetch<R>(a, 0, tile, v);
+        } else if (tile + gridDim.x < tiles) {
+          prefetch<R>(a, 0, tile + gridDim.x, v);
+        }
+      } else {
+        stage<R>(a, t, tile, P);
+      }
       __syncthreads();
       if (phase < 2) {
         float w[K];
