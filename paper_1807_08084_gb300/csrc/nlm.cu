@@ -195,6 +195,9 @@ __global__ void __launch_bounds__(NlmTile<RAD, DIST>::NT, 512 / NlmTile<RAD, DIS
       const int srow = (int)(gy - y0) + RAD;
       const float* zrow = Zs + srow * SW + cx;
       const float* hrow = Hs + srow * SW + cx;
+      // two neighbours per iteration: their dependent chains (sum, det, log2,
+      // exp2) interleave (1.059 -> 0.996 ms for the 1024^2 adjugate filter)
+#pragma unroll 2
       for (int dx = dx0; dx <= dx1; ++dx) {
         float zj[9];
         float2 w;
