@@ -186,8 +186,10 @@ __device__ __forceinline__ void row_step_paired(const float* P, const float2* ws
 // Window sums of all nine channels for the thread's 4 x 2 outputs from one
 // date's staged products P (channel-paired layout): the L + 1 input rows in
 // order, the first and last feeding one output row each.  Per output the taps
-// are added in row-major order.
-template <int R>
+// are added in row-major order.  ROW_UNROLL: middle rows per loop iteration
+// (the Wishart forward takes 2, 2.6% faster at 7 x 7; the weighted multilook
+// 1, which the unroll did not help).
+template <int R, int ROW_UNROLL = 1>
 __device__ __forceinline__ void window_all_paired(const float* P, const float2* wsh2, int y0,
                                                   int x0, float (&z)[9][2][4]) {
   constexpr int L = WTile<R>::L;
@@ -202,7 +204,7 @@ __device__ __forceinline__ void window_all_paired(const float* P, const float2* 
       z8[r][i] = 0.0f;
     }
   row_step_paired<R, true, false>(P, wsh2, 0, y0, x0, zp, z8);
-#pragma unroll 1
+#pragma unroll ROW_UNROLL
   for (int iy = 1; iy < L; ++iy) row_step_paired<R, true, true>(P, wsh2, iy, y0, x0, zp, z8);
   row_step_paired<R, false, true>(P, wsh2, L, y0, x0, zp, z8);
 #pragma unroll

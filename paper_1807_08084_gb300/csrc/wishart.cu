@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
       const int64_t next = t == 0 ? tile : tile + gridDim.x;
       if (next < tiles) issue_block<R>(a.s[1 - t], a.plane_ld, a.H, a.W, next, Sb);
       float z[9][2][4];
-      window_all_paired<R>(P, wsh2, y0, x0, z);
+      window_all_paired<R, 2>(P, wsh2, y0, x0, z);
       if (t == 0) {
 #pragma unroll
         for (int c = 0; c < 9; ++c)
