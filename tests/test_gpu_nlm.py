@@ -344,8 +344,9 @@ def test_stochastic_vs_oracle(zlib, orc, radius, dist, method, h):
           stochastic_bound(z_np, H, W, radius, 16.0, h, dist, ref, 0.7))
 
 
-@pytest.mark.parametrize("dist,h", [(HELLINGER, 0.25), (KULLBACK_LEIBLER, 4.0), (RENYI, 2.0)])
-def test_stochastic_full_size_sampled(zlib, orc, dist, h):
+@pytest.mark.parametrize("dist,h,method", [(HELLINGER, 0.25, 0), (KULLBACK_LEIBLER, 4.0, 0),
+                                           (RENYI, 2.0, 0), (RENYI, 2.0, 1)])
+def test_stochastic_full_size_sampled(zlib, orc, dist, h, method):
     """The benchmark's 1024 x 1024 image, radius 11, in its launch
     configuration: corner, edge and interior pixels against the oracle run on a
     crop holding the pixel's search window."""
@@ -353,7 +354,7 @@ def test_stochastic_full_size_sampled(zlib, orc, dist, h):
     R, N = 11, 1024
     w = S.scaled(S.WORKLOADS["scale_16k"], N, N)
     z = G.packed_z(w)
-    out = zlib.nlm_stochastic(z, R, 16.0, h, dist, 0, order=0.7).reshape(9, N, N)
+    out = zlib.nlm_stochastic(z, R, 16.0, h, dist, method, order=0.7).reshape(9, N, N)
     torch.cuda.synchronize()
     rng = np.random.default_rng(29)
     pts = [(0, 0), (0, N - 1), (N - 1, 0), (N - 1, N - 1), (11, 511), (1012, 3)]
@@ -431,4 +432,20 @@ def test_stochastic_ill_conditioned_vs_oracle(zlib, orc, dist, method, h, order)
     assert np.median(np.abs(ref - z_np).max(axis=0) / np.abs(ref).max(axis=0)) > 1e-3  # it filters
     check(out.reshape(9, -1).cpu().numpy(), ref,
           stochastic_bound(z_np, H, W, 3, 16.0, h, dist, ref, order))
+
+
+@pytest.mark.parametrize("dist,method,h", [(BHATTACHARYYA, 0, 1.0), (BHATTACHARYYA, 1, 1.0),
+                                           (KULLBACK_LEIBLER, 0, 4.0), (RENYI, 0, 2.0)])
+def test_largest_radius_vs_oracle(zlib, orc, dist, method, h):
+    """Radius 15 (31 x 31 windows; Kullback-Leibler's 16-row tiles) on the
+    ragged 37 x 70 image: every output against the oracle."""
+    H, W = 37, 70
+    w = S.scaled(S.WORKLOADS["scale_16k"], H, W)
+    z_np = w.packed_z()
+    z = torch.from_numpy(z_np).cuda().reshape(9, H, W)
+    out = zlib.nlm_stochastic(z, 15, 16.0, h, dist, method, order=0.7)
+    torch.cuda.synchronize()
+    ref = orc.nlm_stochastic(z_np, H, W, 15, 16.0, h, dist, 0.7)
+    check(out.reshape(9, -1).cpu().numpy(), ref,
+          stochastic_bound(z_np, H, W, 15, 16.0, h, dist, ref, 0.7))
 
