@@ -274,7 +274,8 @@ int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int64_t W, int
  * also writes both dates' Z (the forward's window sums, from registers) to
  * z_saved; wishart_stat_bwd_saved takes them instead of recomputing the window
  * sums: a point-wise kernel forms M_t = Z_t^-1 - 2 (Z1 + Z2)^-1 of every pixel
- * (HBM-bound), then a correlation kernel adds the weight gradient.  Same
+ * (three compensated inverses), then a correlation kernel adds the weight
+ * gradient.  Same
  * arithmetic and order as wishart_stat_bwd: the same bits.
  *
  *   z_saved   [18][H*W] device floats (72 bytes per pixel,
