@@ -628,6 +628,10 @@ def main():
                       args.warmup, world)
             nlm[name] = {"ms": t, "gpairs_s": pairs / (t * 1e-3) / 1e9}
         nlm["speedup_adjugate_vs_cholesky"] = nlm["cholesky"]["ms"] / nlm["adjugate"]["ms"]
+        t = timed(lambda: zp.nlm_wishart(zn, 11, 16.0, 1.0, zp.NLM_COMPENSATED, out=zo),
+                  max(3, sub // 5), args.warmup, world)
+        nlm["compensated"] = {"ms": t, "gpairs_s": pairs / (t * 1e-3) / 1e9,
+                              "note": "pair sum kept exact, Dot2 det + first-order term"}
         nlm["workload"] = (f"{wn.H}x{wn.W} packed Z (scale_16k generator), radius 11 "
                            "(23 x 23 window), L = 16, h = 1")
         # the other stochastic distances (nlm_stochastic): Hellinger shares the

@@ -184,7 +184,9 @@ int multilook_zinv_det(const float* s, int64_t H, int64_t W, int64_t plane_ld, i
  *     Z'_i    = sum_j w_ij Z_j / sum_j w_ij.
  * The per-pair determinant is computed by Algorithm 2's cofactor expansion
  * (method 0) or by Algorithm 1's Cholesky route (method 1), so the two can be
- * compared where arithmetic sets the time.
+ * compared where arithmetic sets the time; method 2 is the compensated pair
+ * determinant of nlm_stochastic (ZINV_NLM_COMPENSATED), for ill-conditioned
+ * pixels.
  *
  *   z       [9][ld] packed input (read only), H x W pixels, positive definite.
  *   radius  search radius: 1, 2, 3, 5, 7, 11 (23 x 23 window) or 15.
@@ -215,7 +217,13 @@ int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int radius, fl
  *                             tends to Kullback-Leibler); two determinants per pair.
  *   order     the Renyi order b, in (0, 1); unused by the other distances.
  *   method    the per-pair determinants of Bhattacharyya, Hellinger and Renyi:
- *             ZINV_NLM_ADJUGATE (Algorithm 2) or ZINV_NLM_CHOLESKY (Algorithm 1).
+ *             ZINV_NLM_ADJUGATE (Algorithm 2) or ZINV_NLM_CHOLESKY (Algorithm 1);
+ *             for Bhattacharyya and Hellinger also ZINV_NLM_COMPENSATED:
+ *             Algorithm 2 on the exact pair sum (hi + lo per entry) with Dot2
+ *             cofactors and det plus the first-order term of lo, which keeps
+ *             the weights accurate for ill-conditioned pixels (cond ~1e6,
+ *             where the FP32 rounding of the pair sum alone can move the plain
+ *             det by its own size), at about 3x the plain filter's time.
  *             Kullback-Leibler takes no per-pair determinant and accepts
  *             ZINV_NLM_ADJUGATE only.
  *   z, H, W, ld, radius, looks, h, z_out, stream  as nlm_wishart.
@@ -225,6 +233,7 @@ int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int radius, fl
  */
 #define ZINV_NLM_ADJUGATE 0
 #define ZINV_NLM_CHOLESKY 1
+#define ZINV_NLM_COMPENSATED 2
 #define ZINV_NLM_BHATTACHARYYA 0
 #define ZINV_NLM_HELLINGER 1
 #define ZINV_NLM_KULLBACK_LEIBLER 2

@@ -298,13 +298,15 @@ def zinv_det_blockdiag(z: torch.Tensor, flags: int = PLAIN, tau: float = DEFAULT
 
 NLM_ADJUGATE = 0
 NLM_CHOLESKY = 1
+NLM_COMPENSATED = 2   # Bhattacharyya and Hellinger: compensated pair determinant
 
 
 def nlm_wishart(z: torch.Tensor, radius: int = 11, looks: float = 16.0, h: float = 1.0,
                 method: int = NLM_ADJUGATE, out: torch.Tensor | None = None) -> torch.Tensor:
     """Nonlocal-means filter of a packed [9, H, W] image with the Wishart
     equal-looks distance over a (2 radius + 1)^2 search window; the per-pair
-    determinant by Algorithm 2 (NLM_ADJUGATE) or Algorithm 1 (NLM_CHOLESKY)."""
+    determinant by Algorithm 2 (NLM_ADJUGATE), Algorithm 1 (NLM_CHOLESKY) or
+    compensated Algorithm 2 on the exact pair sum (NLM_COMPENSATED)."""
     lib = load()
     if z.dim() != 3:
         raise ValueError("z must be [9, H, W]")
@@ -334,7 +336,8 @@ def nlm_stochastic(z: torch.Tensor, radius: int = 11, looks: float = 16.0, h: fl
     exp(-d / h), d the Bhattacharyya, Hellinger, Kullback-Leibler or Renyi
     (of `order` in (0, 1)) distance between the pixels' equal-looks Wishart
     laws; the per-pair determinants by Algorithm 2 (NLM_ADJUGATE) or
-    Algorithm 1 (NLM_CHOLESKY), Kullback-Leibler taking none."""
+    Algorithm 1 (NLM_CHOLESKY), for Bhattacharyya and Hellinger also
+    compensated (NLM_COMPENSATED), Kullback-Leibler taking none."""
     lib = load()
     if z.dim() != 3:
         raise ValueError("z must be [9, H, W]")

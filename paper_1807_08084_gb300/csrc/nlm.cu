@@ -104,6 +104,31 @@ __device__ __forceinline__ float det_cholesky(const float x[9]) {
   return q * q;
 }
 
+// sum_k c_k cof_k(x) e_k over the packed entries (c_k = 2 off the diagonal):
+// the first-order change of det(x) when x moves by e (d det = tr(adj dZ)),
+// with the cofactors of Eq. adjoint_elements in plain arithmetic.
+__device__ __forceinline__ float2 det_first_order(const float2 x[9], const float2 e[9]) {
+  const float2 a = x[0], br = x[1], bi = x[2], cr = x[3], ci = x[4];
+  const float2 d = x[5], er = x[6], ei = x[7], f = x[8];
+  const float2 cof[9] = {
+      fma_rn(-er, er, fma_rn(-ei, ei, mul_rn(d, f))),    // a_c
+      fma_rn(-br, f, fma_rn(ci, ei, mul_rn(cr, er))),    // Re b_c
+      fma_rn(-bi, f, fma_rn(-cr, ei, mul_rn(ci, er))),   // Im b_c
+      fma_rn(-cr, d, fma_rn(-bi, ei, mul_rn(br, er))),   // Re c_c
+      fma_rn(-ci, d, fma_rn(bi, er, mul_rn(br, ei))),    // Im c_c
+      fma_rn(-cr, cr, fma_rn(-ci, ci, mul_rn(a, f))),    // d_c
+      fma_rn(-a, er, fma_rn(ci, bi, mul_rn(cr, br))),    // Re e_c
+      fma_rn(-a, ei, fma_rn(-cr, bi, mul_rn(ci, br))),   // Im e_c
+      fma_rn(-br, br, fma_rn(-bi, bi, mul_rn(a, d)))};   // f_c
+  float2 s = mul_rn(cof[0], e[0]);
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    const float two = (k == 5 || k == 8) ? 1.0f : 2.0f;
+    s = fma_rn(mul_rn(make_float2(two, two), cof[k]), e[k], s);
+  }
+  return s;
+}
+
 template <int METHOD, int RAD, int DIST>
 __global__ void __launch_bounds__(NlmTile<RAD, DIST>::NT, 512 / NlmTile<RAD, DIST>::NT)
     k_nlm(NlmArgs a) {
@@ -246,24 +271,42 @@ __global__ void __launch_bounds__(NlmTile<RAD, DIST>::NT, 512 / NlmTile<RAD, DIS
           const float tb = fmaxf(0.5f * (__log2f(D1.y) + __log2f(D2.y)) - (kB + hj), 0.0f);
           w = mul_rn(make_float2(exp2f(np * ta), exp2f(np * tb)), m);
         } else {
-          float2 zs[9];
+          float ta, tb;
+          if constexpr (METHOD == 2) {
+            // compensated: the pair sum exactly as hi + lo, det(hi) by Dot2,
+            // plus the first-order term of lo, sum_k c_k cof_k(hi) lo_k
+            // (c_k = 2 off the diagonal: the gradient of det in packed form)
+            float2 hi[9], lo[9];
 #pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            zj[c] = zrow[c * SH * SW + dx];
-            zs[c] = add_rn(zi[c], make_float2(zj[c], zj[c]));
-          }
-          float2 D;
-          if constexpr (METHOD == 0) {
-            D = det_adjugate<float2>(zs);
+            for (int c = 0; c < 9; ++c) {
+              zj[c] = zrow[c * SH * SW + dx];
+              two_sum(zi[c], make_float2(zj[c], zj[c]), hi[c], lo[c]);
+            }
+            const dd<float2> D = det_comp<float2>(hi);
+            const float2 dlo = add_rn(D.lo, det_first_order(hi, lo));
+            const float hj = hrow[dx];
+            ta = fmaxf(log2f(D.hi.x) + (dlo.x / D.hi.x) * inv_ln2 - (kA + hj), 0.0f);
+            tb = fmaxf(log2f(D.hi.y) + (dlo.y / D.hi.y) * inv_ln2 - (kB + hj), 0.0f);
           } else {
-            float xa[9], xb[9];
+            float2 zs[9];
 #pragma unroll
-            for (int c = 0; c < 9; ++c) xa[c] = zs[c].x, xb[c] = zs[c].y;
-            D = make_float2(det_cholesky(xa), det_cholesky(xb));
+            for (int c = 0; c < 9; ++c) {
+              zj[c] = zrow[c * SH * SW + dx];
+              zs[c] = add_rn(zi[c], make_float2(zj[c], zj[c]));
+            }
+            float2 D;
+            if constexpr (METHOD == 0) {
+              D = det_adjugate<float2>(zs);
+            } else {
+              float xa[9], xb[9];
+#pragma unroll
+              for (int c = 0; c < 9; ++c) xa[c] = zs[c].x, xb[c] = zs[c].y;
+              D = make_float2(det_cholesky(xa), det_cholesky(xb));
+            }
+            const float hj = hrow[dx];
+            ta = fmaxf(__log2f(D.x) - (kA + hj), 0.0f);
+            tb = fmaxf(__log2f(D.y) - (kB + hj), 0.0f);
           }
-          const float hj = hrow[dx];
-          const float ta = fmaxf(__log2f(D.x) - (kA + hj), 0.0f);
-          const float tb = fmaxf(__log2f(D.y) - (kB + hj), 0.0f);
           if constexpr (DIST == kHellinger) {
             // d_H = 1 - 2^(-L t), w = 2^(-(log2 e / h) d_H)
             const float ha = 1.0f - exp2f(nl * ta), hb = 1.0f - exp2f(nl * tb);
@@ -336,8 +379,9 @@ extern "C" int nlm_stochastic(const float* z, int64_t H, int64_t W, int64_t ld, 
       distance != kRenyi)
     return ZINV_ERR_ARG;
   if (distance == kRenyi && !(order > 0.0f && order < 1.0f)) return ZINV_ERR_ARG;
-  if (method != 0 && method != 1) return ZINV_ERR_ARG;
+  if (method != 0 && method != 1 && method != 2) return ZINV_ERR_ARG;
   if (distance == kKullbackLeibler && method != 0) return ZINV_ERR_ARG;  // no pair det
+  if (method == 2 && distance != kBhattacharyya && distance != kHellinger) return ZINV_ERR_ARG;
   if (!z || !z_out || !aligned(z, 4) || !aligned(z_out, 4)) return ZINV_ERR_ARG;
   DeviceInfo di;
   int rc = device_info(&di);
@@ -354,10 +398,13 @@ extern "C" int nlm_stochastic(const float* z, int64_t H, int64_t W, int64_t ld, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (distance) {
     case kBhattacharyya:
-      return method == 0 ? dispatch_nlm<0, kBhattacharyya>(a, s)
-                         : dispatch_nlm<1, kBhattacharyya>(a, s);
+      return method == 0   ? dispatch_nlm<0, kBhattacharyya>(a, s)
+             : method == 1 ? dispatch_nlm<1, kBhattacharyya>(a, s)
+                           : dispatch_nlm<2, kBhattacharyya>(a, s);
     case kHellinger:
-      return method == 0 ? dispatch_nlm<0, kHellinger>(a, s) : dispatch_nlm<1, kHellinger>(a, s);
+      return method == 0   ? dispatch_nlm<0, kHellinger>(a, s)
+             : method == 1 ? dispatch_nlm<1, kHellinger>(a, s)
+                           : dispatch_nlm<2, kHellinger>(a, s);
     case kRenyi:
       return method == 0 ? dispatch_nlm<0, kRenyi>(a, s) : dispatch_nlm<1, kRenyi>(a, s);
     default:

@@ -85,12 +85,13 @@ def test_host_argument_checks():
                              None) == -1  # workspace not 256-byte aligned
     z9 = P(fake)
     # unknown distance, KL with Cholesky, unknown method, Renyi order outside (0, 1)
-    for dist, order, method in ((4, 0.5, 0), (-1, 0.5, 0), (2, 0.5, 1), (1, 0.5, 2),
-                                (3, 0.0, 0), (3, 1.0, 0), (3, float("nan"), 1)):
+    for dist, order, method in ((4, 0.5, 0), (-1, 0.5, 0), (2, 0.5, 1), (1, 0.5, 3),
+                                (2, 0.5, 2), (3, 0.5, 2), (3, 0.0, 0), (3, 1.0, 0),
+                                (3, float("nan"), 1)):
         assert lib.nlm_stochastic(z9, 10, 10, 100, 3, 4.0, 1.0, dist, order, method, z9,
                                   None) == -1
     assert lib.nlm_stochastic(z9, 10, 10, 100, 4, 4.0, 1.0, 0, 0.5, 0, z9, None) == -1  # radius
-    for dist, method in ((0, 0), (1, 1), (2, 0), (3, 1)):
+    for dist, method in ((0, 0), (1, 1), (2, 0), (3, 1), (0, 2), (1, 2)):
         assert lib.nlm_stochastic(z9, 10, 10, 100, 3, 4.0, 1.0, dist, 0.5, method, z9,
                                   None) == -3
     # saved window covariances of the Wishart statistic

@@ -123,7 +123,7 @@ def test_constant_image_is_fixed_point(zlib):
 
 def test_bad_arguments(zlib):
     z = torch.zeros((9, 8, 8), device="cuda")
-    for kw in ({"radius": 4}, {"looks": 0.0}, {"h": -1.0}, {"method": 2}):
+    for kw in ({"radius": 4}, {"looks": 0.0}, {"h": -1.0}, {"method": 3}):
         args = {"radius": 3, "looks": 4.0, "h": 1.0, "method": 0}
         args.update(kw)
         with pytest.raises(RuntimeError):
@@ -192,7 +192,7 @@ def _expansion_magnitude(m):
     return a * (d * f + ae * ae) + ab * (ac * ae + ab * f) + ac * (ab * ae + ac * d)
 
 
-def stochastic_bound(z, H, W, radius, L, h, dist, ref, order=0.5):
+def stochastic_bound(z, H, W, radius, L, h, dist, ref, order=0.5, method=0):
     """[9, H*W] first-order error bound of the FP32 filter with weights
     w_ij = exp(-d_ij / h).  A relative error delta_ij of w_ij moves
     Z'_i = sum_j w_ij Z_j / sum_j w_ij by at most
@@ -217,12 +217,23 @@ def stochastic_bound(z, H, W, radius, L, h, dist, ref, order=0.5):
                       + 9u E(m_k) (E: the expansion in magnitudes);
                       e = (e1 + e2)/2 + 4u (|log2 D1 + log2 D2|/2 + |h_i| + |h_j|),
                       e_k = that / (D_k ln2) + 2^-21, delta = p ln2 (e + u t) + 2^-22
-                      with p = L / ((1-b) h).
+                      with p = L / ((1-b) h);
+      compensated pair det (method 2, Bhattacharyya and Hellinger): the pair sum
+                      is exact (hi + lo); det(hi) by Dot2 (cofactors of three
+                      products, then about ten products with their low parts)
+                      errs by <= u D + 2 gamma_10^2 E, the first-order lo term
+                      by O(u^2 E) more, so
+                      e = (u + 2 gamma_10^2 E / D) / ln2 + 4u (|log2 D| + 3 + |h_i| + |h_j|)
+                      + 2^-22 (log2f and the lo / hi term), then delta as above.
+    The half log-dets h of the determinant-based distances come from the same
+    compensated route on each pixel: each adds (u + 2 gamma_10^2 E_z / D_z) / (2 ln2)
+    to e (negligible beside the plain routes' pair det, not beside method 2's).
     The test bound is 1.25 times the total."""
     Z = np.asarray(z, dtype=np.float64).reshape(9, H, W)
     R = np.asarray(ref, dtype=np.float64).reshape(9, H, W)
     hz = np.abs(np.log2(det3(Z))) / 2
     ldz = np.log(det3(Z))
+    eh = (U + 2 * gamma(10) ** 2 * _expansion_magnitude(np.abs(Z)) / det3(Z)) / (2 * np.log(2))
     if dist == KULLBACK_LEIBLER:
         I, S, dz, Ez = inv3_with_magnitudes(Z)
         dI = 6 * U * np.abs(I) + 2 * gamma(3) ** 2 * (S + Ez * np.abs(I)) / dz
@@ -275,8 +286,13 @@ def stochastic_bound(z, H, W, radius, L, h, dist, ref, order=0.5):
                 det = det3(s)
                 ab, ac, ae = np.abs(br) + np.abs(bi), np.abs(cr) + np.abs(ci), np.abs(er) + np.abs(ei)
                 E = a * (dd * f + ae * ae) + ab * (ac * ae + ab * f) + ac * (ab * ae + ac * dd)
-                e = (gamma(16) * E / (det * np.log(2)) + 2.0 ** -21
-                     + 4 * U * (np.abs(np.log2(det)) + 3 + hz[ys, xs] + hz[yj, xj]))
+                if method == 2:
+                    e = ((U + 2 * gamma(10) ** 2 * E / det) / np.log(2) + 2.0 ** -22
+                         + 4 * U * (np.abs(np.log2(det)) + 3 + hz[ys, xs] + hz[yj, xj]))
+                else:
+                    e = (gamma(16) * E / (det * np.log(2)) + 2.0 ** -21
+                         + 4 * U * (np.abs(np.log2(det)) + 3 + hz[ys, xs] + hz[yj, xj]))
+                e = e + eh[ys, xs] + eh[yj, xj]
                 dB = L * np.maximum(np.log(det / 8) - 0.5 * (ldz[ys, xs] + ldz[yj, xj]), 0)
                 if dist == HELLINGER:
                     xm = np.minimum(1.0, np.exp(-dB) * 2.0 ** np.minimum(L * e, 60.0))
@@ -384,7 +400,8 @@ def test_stochastic_constant_image_is_fixed_point(zlib, dist):
 
 def test_stochastic_bad_arguments(zlib):
     z = torch.zeros((9, 8, 8), device="cuda")
-    for dist, method in ((4, 0), (-1, 0), (KULLBACK_LEIBLER, 1), (HELLINGER, 2)):
+    for dist, method in ((4, 0), (-1, 0), (KULLBACK_LEIBLER, 1), (HELLINGER, 3),
+                         (RENYI, 2)):
         with pytest.raises(RuntimeError):
             zlib.nlm_stochastic(z, 3, 4.0, 1.0, dist, method)
     for order in (0.0, 1.0, -0.5, float("inf")):
@@ -448,4 +465,55 @@ def test_largest_radius_vs_oracle(zlib, orc, dist, method, h):
     ref = orc.nlm_stochastic(z_np, H, W, 15, 16.0, h, dist, 0.7)
     check(out.reshape(9, -1).cpu().numpy(), ref,
           stochastic_bound(z_np, H, W, 15, 16.0, h, dist, ref, 0.7))
+
+
+COMPENSATED = 2
+
+
+@pytest.mark.parametrize("cond", [1e5, 1e6])
+@pytest.mark.parametrize("dist,h", [(BHATTACHARYYA, 1.0), (HELLINGER, 0.25)])
+def test_compensated_ill_conditioned_vs_oracle(zlib, orc, cond, dist, h):
+    """The compensated pair determinant on 16-look covariances of one Sigma
+    with cond 1e5 and 1e6, where the plain route's bounds exceed the data's
+    scale: every output against the oracle under the derived bound."""
+    H, W = 24, 40
+    z_np = ill_conditioned_image(H, W, cond=cond)
+    z = torch.from_numpy(z_np).cuda().reshape(9, H, W)
+    out = zlib.nlm_stochastic(z, 3, 16.0, h, dist, COMPENSATED)
+    torch.cuda.synchronize()
+    ref = orc.nlm_stochastic(z_np, H, W, 3, 16.0, h, dist)
+    assert np.median(np.abs(ref - z_np).max(axis=0) / np.abs(ref).max(axis=0)) > 1e-3
+    bound = stochastic_bound(z_np, H, W, 3, 16.0, h, dist, ref, method=COMPENSATED)
+    assert np.median(bound.max(axis=0) / np.abs(ref).max(axis=0)) < 1e-2  # a real constraint
+    check(out.reshape(9, -1).cpu().numpy(), ref, bound)
+
+
+@pytest.mark.parametrize("radius", [1, 11])
+@pytest.mark.parametrize("dist,h", [(BHATTACHARYYA, 1.0), (HELLINGER, 0.25)])
+def test_compensated_vs_oracle(zlib, orc, radius, dist, h):
+    """The compensated pair determinant on the ragged 37 x 70 class image."""
+    H, W = 37, 70
+    w = S.scaled(S.WORKLOADS["scale_16k"], H, W)
+    z_np = w.packed_z()
+    z = torch.from_numpy(z_np).cuda().reshape(9, H, W)
+    out = zlib.nlm_stochastic(z, radius, 16.0, h, dist, COMPENSATED)
+    torch.cuda.synchronize()
+    ref = orc.nlm_stochastic(z_np, H, W, radius, 16.0, h, dist)
+    check(out.reshape(9, -1).cpu().numpy(), ref,
+          stochastic_bound(z_np, H, W, radius, 16.0, h, dist, ref, method=COMPENSATED))
+
+
+def test_compensated_through_nlm_wishart(zlib):
+    """nlm_wishart's method 2 is nlm_stochastic's compensated Bhattacharyya
+    filter; the other distances refuse method 2."""
+    H, W = 40, 75
+    w = S.scaled(S.WORKLOADS["scale_16k"], H, W)
+    z = torch.from_numpy(w.packed_z()).cuda().reshape(9, H, W)
+    a = zlib.nlm_wishart(z, 5, 16.0, 1.0, COMPENSATED)
+    b = zlib.nlm_stochastic(z, 5, 16.0, 1.0, BHATTACHARYYA, COMPENSATED)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    for dist in (KULLBACK_LEIBLER, RENYI):
+        with pytest.raises(RuntimeError):
+            zlib.nlm_stochastic(z, 5, 16.0, 1.0, dist, COMPENSATED)
 
