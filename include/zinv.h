@@ -223,7 +223,8 @@ int nlm_wishart(const float* z, int64_t H, int64_t W, int64_t ld, int radius, fl
  *             cofactors and det plus the first-order term of lo, which keeps
  *             the weights accurate for ill-conditioned pixels (cond ~1e6,
  *             where the FP32 rounding of the pair sum alone can move the plain
- *             det by its own size), at about 3x the plain filter's time.
+ *             det by its own size), at about 5x the plain filter's time
+ *             (2.3x Algorithm 1's).
  *             Kullback-Leibler takes no per-pair determinant and accepts
  *             ZINV_NLM_ADJUGATE only.
  *   z, H, W, ld, radius, looks, h, z_out, stream  as nlm_wishart.

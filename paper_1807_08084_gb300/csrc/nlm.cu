@@ -285,8 +285,11 @@ __global__ void __launch_bounds__(NlmTile<RAD, DIST>::NT, 512 / NlmTile<RAD, DIS
             const dd<float2> D = det_comp<float2>(hi);
             const float2 dlo = add_rn(D.lo, det_first_order(hi, lo));
             const float hj = hrow[dx];
-            ta = fmaxf(log2f(D.hi.x) + (dlo.x / D.hi.x) * inv_ln2 - (kA + hj), 0.0f);
-            tb = fmaxf(log2f(D.hi.y) + (dlo.y / D.hi.y) * inv_ln2 - (kB + hj), 0.0f);
+            // log2(hi + lo) = log2 hi + lo / (hi ln2) to first order; the lo / hi
+            // term is ~u, so the fast division and log2 (2^-21.4 absolute)
+            // cost nothing against the determinant's own error bound
+            ta = fmaxf(__log2f(D.hi.x) + __fdividef(dlo.x, D.hi.x) * inv_ln2 - (kA + hj), 0.0f);
+            tb = fmaxf(__log2f(D.hi.y) + __fdividef(dlo.y, D.hi.y) * inv_ln2 - (kB + hj), 0.0f);
           } else {
             float2 zs[9];
 #pragma unroll

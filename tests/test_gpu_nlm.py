@@ -224,7 +224,7 @@ def stochastic_bound(z, H, W, radius, L, h, dist, ref, order=0.5, method=0):
                       errs by <= u D + 2 gamma_10^2 E, the first-order lo term
                       by O(u^2 E) more, so
                       e = (u + 2 gamma_10^2 E / D) / ln2 + 4u (|log2 D| + 3 + |h_i| + |h_j|)
-                      + 2^-22 (log2f and the lo / hi term), then delta as above.
+                      + 2^-21 (the fast log2 and the lo / hi term), then delta as above.
     The half log-dets h of the determinant-based distances come from the same
     compensated route on each pixel: each adds (u + 2 gamma_10^2 E_z / D_z) / (2 ln2)
     to e (negligible beside the plain routes' pair det, not beside method 2's).
@@ -287,7 +287,7 @@ def stochastic_bound(z, H, W, radius, L, h, dist, ref, order=0.5, method=0):
                 ab, ac, ae = np.abs(br) + np.abs(bi), np.abs(cr) + np.abs(ci), np.abs(er) + np.abs(ei)
                 E = a * (dd * f + ae * ae) + ab * (ac * ae + ab * f) + ac * (ab * ae + ac * dd)
                 if method == 2:
-                    e = ((U + 2 * gamma(10) ** 2 * E / det) / np.log(2) + 2.0 ** -22
+                    e = ((U + 2 * gamma(10) ** 2 * E / det) / np.log(2) + 2.0 ** -21
                          + 4 * U * (np.abs(np.log2(det)) + 3 + hz[ys, xs] + hz[yj, xj]))
                 else:
                     e = (gamma(16) * E / (det * np.log(2)) + 2.0 ** -21
