@@ -152,11 +152,12 @@ def test_nlm_output(zlib, radius, method):
     out.check(f"nlm radius {radius} method {method}")
 
 
-@pytest.mark.parametrize("dist,method", [(1, 0), (1, 1), (2, 0), (3, 0), (3, 1)])
+@pytest.mark.parametrize("dist,method", [(0, 2), (1, 0), (1, 1), (1, 2), (2, 0), (3, 0), (3, 1)])
 @pytest.mark.parametrize("radius", [2, 11, 15])
 def test_nlm_stochastic_output(zlib, radius, dist, method):
-    """Hellinger, Kullback-Leibler and Renyi weights; Kullback-Leibler runs
-    32-row tiles up to radius 11 and 16-row tiles at 15, both cut by 37 rows."""
+    """Hellinger, Kullback-Leibler and Renyi weights, and the compensated pair
+    determinant; Kullback-Leibler runs 32-row tiles up to radius 11 and 16-row
+    tiles at 15, both cut by 37 rows."""
     lib = zlib.load()
     H, W = 37, 45
     n = H * W
