@@ -152,3 +152,38 @@ def test_binding_rejects_mismatched_outputs():
         zp._out(torch.zeros(9, 4, 4, dtype=torch.float64), (9, 4, 4), z.device, "out")
     with pytest.raises(ValueError):
         zp._out(torch.zeros(9, 4, 5), (9, 4, 4), z.device, "out")
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "zinv.h"
+
+int main(void) {
+    static float buf[64];
+    /* argument errors come back before any device work */
+    int bad = zinv_det(buf, -1, 0, buf, buf, ZINV_PLAIN, 0.0f, NULL, NULL, NULL);
+    int bad_nlm = nlm_stochastic(buf, 4, 4, 16, 3, 4.0f, 1.0f, ZINV_NLM_KULLBACK_LEIBLER,
+                                 0.5f, ZINV_NLM_CHOLESKY, buf, NULL);
+    size_t ws = wishart_workspace_bytes(16, 32, 3);
+    printf("%d %d %d %s %zu\n", zinv_abi_version(), bad, bad_nlm, zinv_status_string(bad), ws);
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/zinv.h compiles as C11 and a C program links against libzinv.so
+    and calls it: the boundary has no C++ or torch types in it."""
+    import subprocess
+    import paper_1807_08084_gb300 as zp
+    lib = Path(zp.load()._name)
+    src = tmp_path / "use_zinv.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use_zinv"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", str(ROOT / "include"),
+                    str(src), "-o", str(exe), "-L", str(lib.parent), "-l:" + lib.name,
+                    "-Wl,-rpath," + str(lib.parent)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert out[0] == "1" and out[1] == "-1" and out[2] == "-1"
+    assert "argument" in " ".join(out[3:-1])
+    assert int(out[-1]) == 1 * 9 * 8  # one 32 x 16 tile, 9 taps, one double each
