@@ -29,10 +29,9 @@
  * stream).  Every call enqueues its work asynchronously on that stream and
  * returns without synchronizing; results are valid once the stream reaches
  * that point.  The device-pointer calls can be captured into a CUDA graph on
- * that stream in relaxed capture mode (they query pointer attributes and set
- * kernel attributes on the host, which global mode forbids); replays give the
- * eager results.  wishart_stat_fwd_noalloc must run once on a device before
- * any capture (it looks up its scratch address then).
+ * that stream (global capture mode included); replays give the eager results.
+ * wishart_stat_fwd_noalloc must run once on a device before any capture (it
+ * looks up its scratch address then).
  *
  * Errors: every int-returning call returns ZINV_OK (0) or a negative code.  An
  * argument error is detected on the host before anything is enqueued.  Nothing

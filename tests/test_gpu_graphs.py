@@ -1,6 +1,5 @@
-"""The entry points inside CUDA graphs: each family is captured (relaxed mode:
-the calls query pointer attributes and set kernel attributes on the host,
-which a global-mode capture forbids), replayed twice, and must give the bits
+"""The entry points inside CUDA graphs: each family is captured in one graph
+(torch's default, global capture mode), replayed twice, and must give the bits
 of the eager calls.  Launch-bound loops (the 256 x 256 latency workload) rely
 on this."""
 import numpy as np
@@ -66,7 +65,7 @@ def test_graph_replay_gives_the_eager_bits(zlib):
     torch.cuda.current_stream().wait_stream(side)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+    with torch.cuda.graph(graph):
         captured = _run(zlib, *args)
         noalloc = torch.empty((), dtype=torch.float64, device="cuda")
         assert zlib.load().wishart_stat_fwd_noalloc(
