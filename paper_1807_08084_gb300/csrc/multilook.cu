@@ -27,11 +27,11 @@
 // the unswizzled 16-byte ring stores: 0.861 -> 0.821 ms at 7 x 7).
 //
 // Weighted windows (general taps, not separable) of 3 x 3, 5 x 5 and 7 x 7 run
-// on the window engine of window.cuh (32 x 16 output tiles, 4 x 2 outputs per
-// thread, two channels per packed FMA, cp.async staging of the next tile
-// behind the window sums); each thread then inverts its own eight outputs from
-// registers and stores four adjacent outputs of a plane with one 128-bit store
-// (parking Z in shared memory for a warp per row of 32 outputs took 6% longer).
+// on the window engines of window.cuh (32 x 16 output tiles, 4 x 2 blocks of
+// outputs, two channels per packed FMA, cp.async staging of the next tile
+// behind the window sums; at 7 x 7 two threads share a block, splitting its
+// channels); each thread then inverts its outputs from registers and stores
+// four adjacent outputs of a plane with one 128-bit store.
 // Other odd windows up to 15 x 15 use a simpler tiled kernel.
 #include "async.cuh"
 #include "common.cuh"
@@ -434,48 +434,77 @@ __global__ void __launch_bounds__(kMlThreads) k_multilook_weighted(MlArgs a) {
   if (STAT && a.counts) add_counts(a.counts, c0, c1);
 }
 
-// Weighted window of 2R + 1 (R = 1..3) on the window engine of window.cuh.
-// Per tile: the staged single-look block's products, the window sums of all
-// nine channels in registers (each output's taps in row-major order, as the
-// simpler kernel adds them), Z parked in shared memory over the products, then
-// per output Algorithm 2 and the stores (a warp covers 32 outputs of a row, so
-// each of the ten output planes is written in full 128-byte rows; inverting
-// each thread's own 4 x 2 outputs from registers instead spread every store
-// over four rows and ran 6-10% slower).
+// Weighted windows of 2R + 1 (R = 1..3) on the window engines of window.cuh.
+// 7 x 7 runs the channel-split engine (128 threads per 32 x 16 tile, two per
+// 4 x 2 block: twice the warps per SM on the same shared memory, 4% faster);
+// 3 x 3 and 5 x 5 the paired engine (64 threads), which the split made 9% and
+// 1% slower, having too few taps to hide its exchange and its duplicated
+// channel-8 loads.
+__host__ __device__ constexpr bool uses_split(int r) { return r == 3; }
+__host__ __device__ constexpr int window_threads(int r) {
+  return uses_split(r) ? win::kWS : win::kWT;
+}
+// Four CTAs per SM; the split engine's FP64-recompute routes need more than
+// its 128 registers and take three (a few bytes of spills, 24% faster than two).
+__host__ __device__ constexpr int window_min_blocks(int r, int alg) {
+  return uses_split(r) && (alg == kPlainF64 || alg == kCompF64) ? 3 : 4;
+}
+
+// Per tile: the staged single-look block's products, the window sums in
+// registers (each output's taps in row-major order, as the simpler kernel adds
+// them), then each thread inverts its outputs with Algorithm 2 -- both rows of
+// its 4 x 2 block (paired engine) or row h of it (split engine) -- and writes
+// four adjacent outputs of a plane with one 128-bit store (parking Z in shared
+// memory for a warp per row of 32 outputs took 6% longer).
 template <int R, int ALG, bool STAT>
-__global__ void __launch_bounds__(win::kWT, 4) k_multilook_window(MlArgs a) {
+__global__ void __launch_bounds__(window_threads(R), window_min_blocks(R, ALG))
+    k_multilook_window(MlArgs a) {
   using T = win::WTile<R>;
-  constexpr int TILE = win::kTH * win::kTW;
+  constexpr bool SPLIT = uses_split(R);
+  constexpr int NT = window_threads(R);
+  constexpr int ROWS = SPLIT ? 1 : 2;  // output rows a thread inverts
   extern __shared__ __align__(16) float smem[];
-  float* P = smem;  // channel-paired products, then the tile's Z [9][TILE]
+  float* P = smem;  // the tile's channel-paired products
   float2* Sb = reinterpret_cast<float2*>(smem + T::P_FLOATS);  // next single-look block
   float2* wsh2 = reinterpret_cast<float2*>(Sb + T::S_F2);      // duplicated taps [L][WROW]
   const int64_t tiles_x = (a.W + win::kTW - 1) / win::kTW;
   const int64_t tiles = tiles_x * ((a.H + win::kTH - 1) / win::kTH);
-  const int y0 = 2 * (threadIdx.x / win::kTX), x0 = 4 * (threadIdx.x % win::kTX);
+  win::Split sp;
+  if (SPLIT) {
+    sp = win::split_of(threadIdx.x);
+  } else {
+    sp = {0, 2 * ((int)threadIdx.x / win::kTX), 4 * ((int)threadIdx.x % win::kTX)};
+  }
   uint32_t c0 = 0, c1 = 0;
   const bool vec = (a.W & 3) == 0 && (reinterpret_cast<uintptr_t>(a.zinv) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(a.det) & 15) == 0;
-  win::stage_taps_paired<R>(a.weights, wsh2);
+  const int64_t n = a.H * a.W;
+  win::stage_taps_paired<R, NT>(a.weights, wsh2);
   if ((int64_t)blockIdx.x < tiles)
-    win::issue_block<R>(a.s, a.plane_ld, a.H, a.W, blockIdx.x, Sb);
+    win::issue_block<R, NT>(a.s, a.plane_ld, a.H, a.W, blockIdx.x, Sb);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * win::kTH, tx0 = (tile % tiles_x) * win::kTW;
     cp_async_wait<0>();
-    __syncthreads();  // the block is in Sb; P is free (the last tile's Z is read)
-    win::block_products_paired<R>(Sb, P);
+    __syncthreads();  // the block is in Sb; the last tile's window sums are done with P
+    win::block_products_paired<R, NT>(Sb, P);
     __syncthreads();  // Sb is free; P holds the products
     const int64_t next = tile + gridDim.x;
-    if (next < tiles) win::issue_block<R>(a.s, a.plane_ld, a.H, a.W, next, Sb);
-    float z[9][2][4];
-    win::window_all_paired<R>(P, wsh2, y0, x0, z);
-    // each thread inverts its own 4 x 2 outputs from registers and stores
-    // four adjacent outputs of a plane with one 128-bit store
-    const int64_t n = a.H * a.W;
-    const int64_t gx = tx0 + x0;
+    if (next < tiles) win::issue_block<R, NT>(a.s, a.plane_ld, a.H, a.W, next, Sb);
+    float z[9][ROWS][4];
+    if constexpr (SPLIT) {
+      float zr[9][4];
+      win::window_split<R>(P, wsh2, sp, zr);
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int64_t gy = ty0 + y0 + r;
+      for (int c = 0; c < 9; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) z[c][0][i] = zr[c][i];
+    } else {
+      win::window_all_paired<R>(P, wsh2, sp.y0, sp.x0, z);
+    }
+    const int64_t gx = tx0 + sp.x0;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const int64_t gy = ty0 + sp.y0 + (SPLIT ? sp.h : r);
       float4 wv[9], dv;
       uint32_t stv[4];
 #pragma unroll
@@ -525,15 +554,15 @@ constexpr size_t window_smem() {
 }
 
 template <typename K>
-int launch_window(K kernel, size_t smem, const MlArgs& a, cudaStream_t s) {
+int launch_window(K kernel, size_t smem, int threads, const MlArgs& a, cudaStream_t s) {
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return ZINV_ERR_LAUNCH;
   }
   const int64_t tiles = ((a.W + win::kTW - 1) / win::kTW) * ((a.H + win::kTH - 1) / win::kTH);
-  const int64_t blocks = cover_blocks(tiles * win::kWT, win::kWT);
-  kernel<<<(unsigned)blocks, win::kWT, smem, s>>>(a);
+  const int64_t blocks = cover_blocks(tiles * threads, threads);
+  kernel<<<(unsigned)blocks, threads, smem, s>>>(a);
   return launch_status();
 }
 
@@ -568,9 +597,12 @@ template <int ALG, bool STAT>
 int dispatch_ml(const MlArgs& a, cudaStream_t s) {
   if (a.weights) {
     switch (a.win) {
-      case 3: return launch_window(k_multilook_window<1, ALG, STAT>, window_smem<1>(), a, s);
-      case 5: return launch_window(k_multilook_window<2, ALG, STAT>, window_smem<2>(), a, s);
-      case 7: return launch_window(k_multilook_window<3, ALG, STAT>, window_smem<3>(), a, s);
+      case 3: return launch_window(k_multilook_window<1, ALG, STAT>, window_smem<1>(),
+                                   window_threads(1), a, s);
+      case 5: return launch_window(k_multilook_window<2, ALG, STAT>, window_smem<2>(),
+                                   window_threads(2), a, s);
+      case 7: return launch_window(k_multilook_window<3, ALG, STAT>, window_smem<3>(),
+                                   window_threads(3), a, s);
     }
     return launch_ml(k_multilook_weighted<ALG, STAT>, kWSmem, a, s);
   }

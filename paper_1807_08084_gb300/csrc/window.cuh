@@ -8,8 +8,10 @@
 // (the packed entries of s s^H) go to P in the channel-paired layout below;
 // window_all_paired sums a (2R+1)^2 window of them for all nine channels, the
 // input rows as the outer loop, with each output's taps added in row-major
-// order, two channels per packed f32x2 FMA.  (The Wishart backward keeps the
-// scalar layout P [9][SH][SWP] and sums one channel at a time.)
+// order, two channels per packed f32x2 FMA.  window_split is the same sums
+// with two threads per 4 x 2 block (128 per tile), each on half the channels.
+// (The Wishart backward keeps the scalar layout P [9][SH][SWP] and sums one
+// channel at a time.)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -76,13 +78,13 @@ __device__ __forceinline__ void load_row(const float* src, float (&row)[4 * WTil
 // Issues, as one cp.async group, the copies of an image's single-look block of
 // a tile plus halo (clamp-to-edge) into Sb [3][SH][SW]; s holds the three
 // component planes of an H x W image, plane_ld apart.
-template <int R>
+template <int R, int NT = kWT>
 __device__ __forceinline__ void issue_block(const float2* s, int64_t plane_ld, int64_t H,
                                             int64_t W, int64_t tile, float2* Sb) {
   using T = WTile<R>;
   const int64_t tiles_x = (W + kTW - 1) / kTW;
   const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
-  for (int i = threadIdx.x; i < T::SH * T::SW; i += kWT) {
+  for (int i = threadIdx.x; i < T::SH * T::SW; i += NT) {
     const int r = i / T::SW, x = i - r * T::SW;
     const int64_t q = clampi(ty0 - R + r, H - 1) * W + clampi(tx0 - R + x, W - 1);
 #pragma unroll
@@ -102,11 +104,11 @@ __device__ __forceinline__ void issue_block(const float2* s, int64_t plane_ld, i
 __device__ __forceinline__ int pcol(int x) { return x ^ ((x >> 3) & 2); }
 
 // The nine channel products of the staged block Sb in the channel-paired layout.
-template <int R>
+template <int R, int NT = kWT>
 __device__ __forceinline__ void block_products_paired(const float2* Sb, float* P) {
   using T = WTile<R>;
   float2* P2 = reinterpret_cast<float2*>(P);
-  for (int i = threadIdx.x; i < T::SH * T::SW; i += kWT) {
+  for (int i = threadIdx.x; i < T::SH * T::SW; i += NT) {
     const int r = i / T::SW, x = i - r * T::SW;
     float p[9];
     products(Sb[i], Sb[T::SH * T::SW + i], Sb[2 * T::SH * T::SW + i], p);
@@ -119,10 +121,10 @@ __device__ __forceinline__ void block_products_paired(const float2* Sb, float* P
 
 // Copies the taps, each duplicated into both halves of a float2, into the
 // shared table [L][WROW] of float2 (the packed FMAs' weight operand).
-template <int R>
+template <int R, int NT = kWT>
 __device__ __forceinline__ void stage_taps_paired(const float* weights, float2* wsh2) {
   using T = WTile<R>;
-  for (int k = threadIdx.x; k < T::K; k += kWT) {
+  for (int k = threadIdx.x; k < T::K; k += NT) {
     const float w = weights[k];
     wsh2[(k / T::L) * T::WROW + k % T::L] = make_float2(w, w);
   }
@@ -218,6 +220,125 @@ __device__ __forceinline__ void window_all_paired(const float* P, const float2* 
       }
       z[8][r][i] = z8[r][i];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Channel-split engine: two threads per 4 x 2 block of outputs, 128 per tile.
+// Lanes l and l ^ 8 of a warp share a block; half h = (l >> 3) & 1 sums
+// channel pairs 2h and 2h + 1 for both output rows and channel 8 for output
+// row h alone, so both halves issue the same FMAs (per tap: eight packed ones
+// and four scalar ones), and each quarter-warp reads one plane, as in the
+// paired engine.  Every accumulator adds its taps in the same order as the
+// paired engine: the sums are the same bits.  After the sums the halves swap
+// the pairs of the other's row with one shuffle each, so half h holds all nine
+// channels of row h.  Twice the threads on the same shared memory doubles the
+// warps per SM.
+constexpr int kWS = 2 * kWT;  // threads per CTA of the split engine
+
+struct Split {
+  int h;       // channel pairs 2h, 2h + 1; channel 8 and the inverses of output row h
+  int y0, x0;  // the block: output rows y0, y0 + 1, columns x0 .. x0 + 3
+};
+
+__device__ __forceinline__ Split split_of(int t) {
+  const int lane = t & 31;
+  const int b = 16 * (t >> 5) + (lane & 7) + 8 * (lane >> 4);  // block 0..63
+  return {(lane >> 3) & 1, 2 * (b / kTX), 4 * (b % kTX)};
+}
+
+// One input row for a half block: row y0 + iy feeds output row 0 with tap row
+// iy (ROW0) and output row 1 with tap row iy - 1 (ROW1), as row_step_paired.
+template <int R, bool ROW0, bool ROW1>
+__device__ __forceinline__ void row_step_split(const float* P, const float2* wsh2, int iy,
+                                               const Split& sp, float2 (&zp)[2][2][4],
+                                               float (&z8)[4]) {
+  using T = WTile<R>;
+  constexpr int L = T::L;
+  constexpr int NU = 2 + R;
+  float2 w0[L + 1], w1[L + 1];
+#pragma unroll
+  for (int h = 0; h < (L + 1) / 2; ++h) {
+    if (ROW0) {
+      const float4 q = *reinterpret_cast<const float4*>(wsh2 + iy * T::WROW + 2 * h);
+      w0[2 * h] = make_float2(q.x, q.y), w0[2 * h + 1] = make_float2(q.z, q.w);
+    }
+    if (ROW1) {
+      const float4 q = *reinterpret_cast<const float4*>(wsh2 + (iy - 1) * T::WROW + 2 * h);
+      w1[2 * h] = make_float2(q.x, q.y), w1[2 * h + 1] = make_float2(q.z, q.w);
+    }
+  }
+  const float2* src =
+      reinterpret_cast<const float2*>(P) + 2 * sp.h * T::PLANE + (sp.y0 + iy) * T::SWP;
+#pragma unroll
+  for (int jj = 0; jj < 2; ++jj) {
+    float2 row[2 * NU];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) {
+      const float4 v =
+          *reinterpret_cast<const float4*>(src + jj * T::PLANE + pcol(sp.x0 + 2 * q));
+      row[2 * q] = make_float2(v.x, v.y);
+      row[2 * q + 1] = make_float2(v.z, v.w);
+    }
+#pragma unroll
+    for (int dx = 0; dx < L; ++dx)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (ROW0) zp[jj][0][i] = __ffma2_rn(w0[dx], row[i + dx], zp[jj][0][i]);
+        if (ROW1) zp[jj][1][i] = __ffma2_rn(w1[dx], row[i + dx], zp[jj][1][i]);
+      }
+  }
+  // channel 8 of output row h: tap row iy - h; the first input row feeds only
+  // row 0, the last only row 1
+  if ((ROW0 && ROW1) || (ROW0 ? sp.h == 0 : sp.h == 1)) {
+    float row[4 * T::NV];
+    load_row<R>(P + 8 * T::PLANE + (sp.y0 + iy) * T::SWP + sp.x0, row);
+#pragma unroll
+    for (int dx = 0; dx < L; ++dx) {
+      const float w = (ROW0 && ROW1) ? (sp.h ? w1[dx].x : w0[dx].x) : (ROW0 ? w0[dx].x : w1[dx].x);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) z8[i] = fmaf(w, row[i + dx], z8[i]);
+    }
+  }
+}
+
+// Window sums of all nine channels for output row y0 + h of the half block's
+// 4 x 2 outputs (z[c][i]: channel c, column x0 + i).  Every lane of the warp
+// must call it (the exchange is a full-warp shuffle).
+template <int R, int ROW_UNROLL = 1>
+__device__ __forceinline__ void window_split(const float* P, const float2* wsh2, const Split& sp,
+                                             float (&z)[9][4]) {
+  constexpr int L = WTile<R>::L;
+  float2 zp[2][2][4];
+  float z8[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) zp[jj][0][i] = zp[jj][1][i] = make_float2(0.0f, 0.0f);
+    z8[i] = 0.0f;
+  }
+  row_step_split<R, true, false>(P, wsh2, 0, sp, zp, z8);
+#pragma unroll ROW_UNROLL
+  for (int iy = 1; iy < L; ++iy) row_step_split<R, true, true>(P, wsh2, iy, sp, zp, z8);
+  row_step_split<R, false, true>(P, wsh2, L, sp, zp, z8);
+  // half h keeps its pairs of row h and gives its pairs of the other row; it
+  // receives the partner's pairs of row h
+#pragma unroll
+  for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 keep = sp.h ? zp[jj][1][i] : zp[jj][0][i];
+      const float2 give = sp.h ? zp[jj][0][i] : zp[jj][1][i];
+      const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, give.x, 8),
+                                     __shfl_xor_sync(0xffffffffu, give.y, 8));
+      const float2 lo = sp.h ? got : keep;  // pair jj: channels 2 jj, 2 jj + 1
+      const float2 hi = sp.h ? keep : got;  // pair 2 + jj: channels 4 + 2 jj, 5 + 2 jj
+      z[2 * jj][i] = lo.x;
+      z[2 * jj + 1][i] = lo.y;
+      z[4 + 2 * jj][i] = hi.x;
+      z[5 + 2 * jj][i] = hi.y;
+    }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) z[8][i] = z8[i];
 }
 
 // Stores the thread's 4 x 2 block of one channel into a [kTH][kTW] plane.
