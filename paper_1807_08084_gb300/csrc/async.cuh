@@ -23,6 +23,15 @@ __device__ __forceinline__ void cp_async4_zfill(void* smem_dst, const void* gmem
                "r"(valid ? 4 : 0)
                : "memory");
 }
+// 16-byte copy that writes zeros instead (reading nothing) when !valid; both
+// addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gmem_src,
+                                                 bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem_src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
 // Closes the group of copies issued so far by this thread.
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");

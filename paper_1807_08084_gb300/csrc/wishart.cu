@@ -60,6 +60,7 @@ struct WsArgs {
   float* z_save = nullptr;   // forward: both dates' Z, [18][H*W], or null
   bool z_vec = false;        // z_save takes 16-byte stores (16-byte aligned, W % 4 == 0)
   const float* m = nullptr;  // saved-Z backward: the packed M_1, M_2, [18][H*W]
+  bool m_vec = false;        // m takes 16-byte copies (16-byte aligned, W % 4 == 0)
 };
 
 // Loads into registers the three components of the staged pixels this thread
@@ -367,6 +368,64 @@ __device__ __forceinline__ void bwd_inverses(const WsArgs& a, float* G, int64_t 
   }
 }
 
+// One thread's weight-gradient tap accumulators: tap (dy, dx) with dx < L - 1
+// in the float2 pair (dx even, dx + 1), the last column dx = L - 1 scalar.
+template <int R>
+struct TapAcc {
+  static constexpr int L = 2 * R + 1;
+  float2 p[L][R];
+  float s[L];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int dy = 0; dy < L; ++dy) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) p[dy][j] = make_float2(0.0f, 0.0f);
+      s[dy] = 0.0f;
+    }
+  }
+  // tap k = dy L + dx (k a compile-time constant after unrolling)
+  __device__ __forceinline__ float get(int k) const {
+    const int dy = k / L, dx = k - (k / L) * L;
+    return dx == L - 1 ? s[dy] : ((dx & 1) ? p[dy][dx >> 1].y : p[dy][dx >> 1].x);
+  }
+};
+
+// The correlation terms of one staged input row (row y0 + iy of the thread's
+// columns x0 .. x0 + 3 + 2R): tap (dy, dx) += g[r][i] row[i + dx] for output
+// rows r with dy = iy - r, each tap's terms in order i = 0..3.  For even i the
+// pair (row[i + dx], row[i + dx + 1]) of an even dx is an aligned pair of the
+// loaded row, so one packed f32x2 FMA adds to both taps of a pair (each half
+// rounded as the scalar fmaf: the bits of the scalar loop); odd i and the last
+// column take scalar FMAs.
+template <int R>
+__device__ __forceinline__ void corr_row(const float (&g)[2][4],
+                                         const float (&row)[4 * WTile<R>::NV], int iy,
+                                         TapAcc<R>& acc) {
+  constexpr int L = 2 * R + 1;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int dy = iy - r;
+    if (dy < 0 || dy >= L) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if ((i & 1) == 0) {
+        const float2 gg = make_float2(g[r][i], g[r][i]);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          acc.p[dy][j] =
+              __ffma2_rn(gg, make_float2(row[i + 2 * j], row[i + 2 * j + 1]), acc.p[dy][j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          acc.p[dy][j].x = fmaf(g[r][i], row[i + 2 * j], acc.p[dy][j].x);
+          acc.p[dy][j].y = fmaf(g[r][i], row[i + 2 * j + 1], acc.p[dy][j].y);
+        }
+      }
+      acc.s[dy] = fmaf(g[r][i], row[i + L - 1], acc.s[dy]);
+    }
+  }
+}
+
 template <int R>
 __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
   using T = WTile<R>;
@@ -395,9 +454,8 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
   }
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
-    float acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
+    TapAcc<R> acc;
+    acc.zero();
 #pragma unroll 1
     for (int phase = 0; phase < 3; ++phase) {
       const int t = phase == 1 ? 1 : 0;  // the date staged now
@@ -451,16 +509,7 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
           for (int iy = 0; iy <= L; ++iy) {
             float row[4 * T::NV];
             load_row<R>(Pc + (y0 + iy) * T::SWP + x0, row);
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-              const int dy = iy - r;
-              if (dy < 0 || dy >= L) continue;
-#pragma unroll
-              for (int dx = 0; dx < L; ++dx)
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                  acc[dy * L + dx] = fmaf(g[r][i], row[i + dx], acc[dy * L + dx]);
-            }
+            corr_row<R>(g, row, iy, acc);
           }
         }
       }
@@ -474,7 +523,7 @@ __global__ void __launch_bounds__(kWT, 3) k_wishart_bwd(WsArgs a) {
     __syncthreads();
     float* accs = P;
 #pragma unroll
-    for (int k = 0; k < K; ++k) accs[k * (kWT + 1) + threadIdx.x] = acc[k];
+    for (int k = 0; k < K; ++k) accs[k * (kWT + 1) + threadIdx.x] = acc.get(k);
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += kWT) {
       float sum = 0.0f, err = 0.0f;
@@ -555,20 +604,32 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_corr(WsArgs a) {
   if ((int64_t)blockIdx.x < tiles) prefetch<R>(a, 1, blockIdx.x, v);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
-    float acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
+    TapAcc<R> acc;
+    acc.zero();
 #pragma unroll 1
     for (int t = 1; t >= 0; --t) {
       __syncthreads();
       // M_t of the tile (zero outside the image) copied asynchronously while
       // the products are formed
+      if (a.m_vec) {
+        // 16-byte groups: with W % 4 == 0 the four outputs of a group are all
+        // inside the image or all outside
+#pragma unroll 2
+        for (int e = threadIdx.x; e < 9 * TILE / 4; e += kWT) {
+          const int c = e / (TILE / 4), o = 4 * (e - c * (TILE / 4));
+          const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
+          const bool in = gy < a.H && gx < a.W;
+          cp_async16_zfill(G + c * TILE + o, in ? a.m + (9 * t + c) * n + gy * a.W + gx : a.m,
+                           in);
+        }
+      } else {
 #pragma unroll 8
-      for (int e = threadIdx.x; e < 9 * TILE; e += kWT) {
-        const int c = e / TILE, o = e - c * TILE;
-        const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
-        const bool in = gy < a.H && gx < a.W;
-        cp_async4_zfill(G + e, in ? a.m + (9 * t + c) * n + gy * a.W + gx : a.m, in);
+        for (int e = threadIdx.x; e < 9 * TILE; e += kWT) {
+          const int c = e / TILE, o = e - c * TILE;
+          const int64_t gy = ty0 + o / kTW, gx = tx0 + o % kTW;
+          const bool in = gy < a.H && gx < a.W;
+          cp_async4_zfill(G + e, in ? a.m + (9 * t + c) * n + gy * a.W + gx : a.m, in);
+        }
       }
       cp_async_commit();
       store_products<R>(v, P);
@@ -596,16 +657,7 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_corr(WsArgs a) {
         for (int iy = 0; iy <= L; ++iy) {
           float row[4 * T::NV];
           load_row<R>(Pc + (y0 + iy) * T::SWP + x0, row);
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int dy = iy - r;
-            if (dy < 0 || dy >= L) continue;
-#pragma unroll
-            for (int dx = 0; dx < L; ++dx)
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-                acc[dy * L + dx] = fmaf(g[r][i], row[i + dx], acc[dy * L + dx]);
-          }
+          corr_row<R>(g, row, iy, acc);
         }
       }
     }
@@ -613,7 +665,7 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_corr(WsArgs a) {
     __syncthreads();
     float* accs = P;
 #pragma unroll
-    for (int k = 0; k < K; ++k) accs[k * (kWT + 1) + threadIdx.x] = acc[k];
+    for (int k = 0; k < K; ++k) accs[k * (kWT + 1) + threadIdx.x] = acc.get(k);
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += kWT) {
       float sum = 0.0f, err = 0.0f;
@@ -842,6 +894,7 @@ extern "C" int wishart_stat_bwd_saved(const float* s1, const float* s2, int64_t 
     return ZINV_ERR_ARG;
   float* m = reinterpret_cast<float*>(static_cast<char*>(ws) + partials_bytes(H, W, win));
   a.m = m;
+  a.m_vec = aligned(m, 16) && (W % 4) == 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = H * W;
   k_wishart_m<<<(unsigned)cover_blocks((n + 1) / 2, 256), 256, 0, st>>>(z_saved, m, n);
