@@ -15,20 +15,21 @@
 // with strongly correlated channels det / (a d f) falls to a few 10^-3, where
 // the plain expansion loses most of its digits.
 //
-// Tiles of 32 x 16 outputs, 64 threads, each thread a block of 4 x 2 outputs,
-// so each input row a thread loads from shared memory feeds both of its output
-// rows (2 x 4 x win FMAs per loaded row).  One date's channel products for the
-// tile and its halo sit in shared memory at a time.
+// Tiles of 32 x 16 outputs in blocks of 4 x 2 outputs, so each input row a
+// thread loads from shared memory feeds both output rows of its block
+// (2 x 4 x win FMAs per loaded row).  One date's channel products for the tile
+// and its halo sit in shared memory at a time.
 //   Forward: each date's single-look block is copied with cp.async while the
 //   other date's window sums run; the window is summed with the input rows as
-//   the outer loop and the nine channels unrolled, two channels per packed
-//   f32x2 FMA (window_all_paired of window.cuh; Z in registers); date 1's Z
-//   stays in registers while date 2's is summed, and each thread then takes
-//   the log-dets of its own eight outputs from registers, two adjacent
-//   outputs per pass with the compensated arithmetic on packed float2 pairs
-//   (f32x2: one instruction for both, each half rounded as the scalar
-//   operation).  ~52 KB of shared memory per CTA, four CTAs per SM.
-//   Backward: blocks are loaded directly; the window is summed one channel at a
+//   the outer loop, two channels per packed f32x2 FMA, by 128 threads per tile,
+//   two per block each summing half the channels (window_split of window.cuh;
+//   Z in registers); date 1's Z stays in registers while date 2's is summed,
+//   and each thread then takes the log-dets of the four outputs of its row
+//   from registers, two adjacent outputs per pass with the compensated
+//   arithmetic on packed float2 pairs (f32x2: one instruction for both, each
+//   half rounded as the scalar operation).  ~52 KB of shared memory per CTA,
+//   four CTAs per SM.
+//   Backward (64 threads per tile, one per block): blocks are loaded directly; the window is summed one channel at a
 //   time (the registers go to the 49 tap accumulators); Z, then the packed
 //   M_t, are parked in shared memory for the correlations; the inverses run
 //   as packed pairs where registers allow (3 x 3 and 5 x 5 windows).
@@ -156,37 +157,6 @@ __device__ __forceinline__ void stage(const WsArgs& a, int t, int64_t tile, floa
   store_products<R>(v, P);
 }
 
-// Both dates' Z of the thread's 4 x 2 outputs (rows y0, y0 + 1, columns
-// x0 .. x0 + 3 of the tile) -> z_save: date 1's nine packed planes, then date
-// 2's, plane stride H*W.  Outputs outside the image are not stored.
-__device__ __forceinline__ void save_z(const WsArgs& a, int64_t ty0, int64_t tx0, int y0, int x0,
-                                       const float (&z1)[9][2][4], const float (&z2)[9][2][4]) {
-  const int64_t n = a.H * a.W, gx = tx0 + x0;
-  const bool vec = a.z_vec && gx + 4 <= a.W;
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int64_t gy = ty0 + y0 + r;
-    if (gy >= a.H) continue;
-    float* base = a.z_save + gy * a.W + gx;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      if (vec) {
-        __stcs(reinterpret_cast<float4*>(base + c * n),
-               make_float4(z1[c][r][0], z1[c][r][1], z1[c][r][2], z1[c][r][3]));
-        __stcs(reinterpret_cast<float4*>(base + (9 + c) * n),
-               make_float4(z2[c][r][0], z2[c][r][1], z2[c][r][2], z2[c][r][3]));
-      } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (gx + i < a.W) {
-            __stcs(base + c * n + i, z1[c][r][i]);
-            __stcs(base + (9 + c) * n + i, z2[c][r][i]);
-          }
-      }
-    }
-  }
-}
-
 // Fixed-order block reduction of one double per thread; returns the sum in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
@@ -201,8 +171,45 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Both dates' Z of one output row (tile row yr, columns x0 .. x0 + 3) ->
+// z_save: date 1's nine packed planes, then date 2's, plane stride H*W.
+// Outputs outside the image are not stored.
+__device__ __forceinline__ void save_z_row(const WsArgs& a, int64_t ty0, int64_t tx0, int yr,
+                                           int x0, const float (&z1)[9][4],
+                                           const float (&z2)[9][4]) {
+  const int64_t n = a.H * a.W, gx = tx0 + x0, gy = ty0 + yr;
+  if (gy >= a.H) return;
+  const bool vec = a.z_vec && gx + 4 <= a.W;
+  float* base = a.z_save + gy * a.W + gx;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    if (vec) {
+      __stcs(reinterpret_cast<float4*>(base + c * n),
+             make_float4(z1[c][0], z1[c][1], z1[c][2], z1[c][3]));
+      __stcs(reinterpret_cast<float4*>(base + (9 + c) * n),
+             make_float4(z2[c][0], z2[c][1], z2[c][2], z2[c][3]));
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (gx + i < a.W) {
+          __stcs(base + c * n + i, z1[c][i]);
+          __stcs(base + (9 + c) * n + i, z2[c][i]);
+        }
+    }
+  }
+}
+
+// The forward runs the channel-split window engine (128 threads per tile, two
+// per 4 x 2 block of outputs, each summing half the channels), four CTAs per
+// SM: 16 warps with 4 tiles in flight, against 8 warps on the paired engine
+// (3 x 3 / 5 x 5 13% / 9% faster, 7 x 7 unchanged, same bits).  The saving
+// 7 x 7 forward, with its Z stores, runs three CTAs with more registers (2%).
+__host__ __device__ constexpr int fwd_min_blocks(int r, bool save) {
+  return save && r == 3 ? 3 : 4;
+}
+
 template <int R, bool SAVE>
-__global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
+__global__ void __launch_bounds__(kWS, fwd_min_blocks(R, SAVE)) k_wishart_fwd(WsArgs a) {
   using T = WTile<R>;
   extern __shared__ __align__(16) float smem[];
   float* P = smem;  // one date's products, channel-paired layout
@@ -211,64 +218,60 @@ __global__ void __launch_bounds__(kWT, 4) k_wishart_fwd(WsArgs a) {
   double* red = reinterpret_cast<double*>(wsh2 + T::L * T::WROW);
   const int64_t tiles_x = (a.W + kTW - 1) / kTW;
   const int64_t tiles = tiles_x * ((a.H + kTH - 1) / kTH);
-  const int y0 = 2 * (threadIdx.x / kTX), x0 = 4 * (threadIdx.x % kTX);
+  const Split sp = split_of(threadIdx.x);
   const float six_ln2 = 4.15888308335967185650f;
-  stage_taps_paired<R>(a.weights, wsh2);
-  if ((int64_t)blockIdx.x < tiles) issue_block<R>(a.s[0], a.plane_ld, a.H, a.W, blockIdx.x, Sb);
+  stage_taps_paired<R, kWS>(a.weights, wsh2);
+  if ((int64_t)blockIdx.x < tiles)
+    issue_block<R, kWS>(a.s[0], a.plane_ld, a.H, a.W, blockIdx.x, Sb);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t ty0 = (tile / tiles_x) * kTH, tx0 = (tile % tiles_x) * kTW;
-    float z0[9][2][4];  // date 1's Z of the thread's 4 x 2 outputs
+    float z0[9][4];  // date 1's Z of the thread's output row
     double qsum = 0.0;
 #pragma unroll 1
     for (int t = 0; t < 2; ++t) {
       cp_async_wait<0>();
       __syncthreads();  // date t's block is in Sb; P is free (and the taps are in place)
-      block_products_paired<R>(Sb, P);
+      block_products_paired<R, kWS>(Sb, P);
       __syncthreads();  // Sb is free; P holds date t's products
       // the next block (date 2 of this tile, then date 1 of the next) loads
       // while this date's window sums run
       const int64_t next = t == 0 ? tile : tile + gridDim.x;
-      if (next < tiles) issue_block<R>(a.s[1 - t], a.plane_ld, a.H, a.W, next, Sb);
-      float z[9][2][4];
-      window_all_paired<R, 2>(P, wsh2, y0, x0, z);
+      if (next < tiles) issue_block<R, kWS>(a.s[1 - t], a.plane_ld, a.H, a.W, next, Sb);
+      float z[9][4];
+      window_split<R, 2>(P, wsh2, sp, z);
       if (t == 0) {
 #pragma unroll
         for (int c = 0; c < 9; ++c)
 #pragma unroll
-          for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) z0[c][r][i] = z[c][r][i];
+          for (int i = 0; i < 4; ++i) z0[c][i] = z[c][i];
         continue;
       }
-      if constexpr (SAVE) save_z(a, ty0, tx0, y0, x0, z0, z);
-      // Both dates' Z are in registers: the thread takes the compensated
-      // log-dets of Z1, Z2 and Z1 + Z2 of its own 4 x 2 outputs, two adjacent
-      // outputs per pass on packed float2 pairs, and stores and adds its q in
-      // row-major order.
+      if constexpr (SAVE) save_z_row(a, ty0, tx0, sp.y0 + sp.h, sp.x0, z0, z);
+      // Both dates' Z of row h are in registers: the thread takes the
+      // compensated log-dets of Z1, Z2 and Z1 + Z2 of its four outputs, two
+      // adjacent outputs per pass on packed float2 pairs, and stores and adds
+      // its q in column order.
+      const int64_t gy = ty0 + sp.y0 + sp.h;
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int64_t gy = ty0 + y0 + r;
+      for (int i = 0; i < 4; i += 2) {
+        float2 z1[9], z2[9], z12[9];
 #pragma unroll
-        for (int i = 0; i < 4; i += 2) {
-          float2 z1[9], z2[9], z12[9];
+        for (int c = 0; c < 9; ++c) {
+          z1[c] = make_float2(z0[c][i], z0[c][i + 1]);
+          z2[c] = make_float2(z[c][i], z[c][i + 1]);
+          z12[c] = add_rn(z1[c], z2[c]);
+        }
+        const float2 l1 = log_dd(det_comp<float2>(z1));
+        const float2 l2 = log_dd(det_comp<float2>(z2));
+        const float2 l12 = log_dd(det_comp<float2>(z12));
 #pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            z1[c] = make_float2(z0[c][r][i], z0[c][r][i + 1]);
-            z2[c] = make_float2(z[c][r][i], z[c][r][i + 1]);
-            z12[c] = add_rn(z1[c], z2[c]);
-          }
-          const float2 l1 = log_dd(det_comp<float2>(z1));
-          const float2 l2 = log_dd(det_comp<float2>(z2));
-          const float2 l12 = log_dd(det_comp<float2>(z12));
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int64_t gx = tx0 + x0 + i + e;
-            if (gy >= a.H || gx >= a.W) continue;
-            const float q = e == 0 ? (l1.x + l2.x) - 2.0f * l12.x + six_ln2
-                                   : (l1.y + l2.y) - 2.0f * l12.y + six_ln2;
-            if (a.q_map) a.q_map[gy * a.W + gx] = q;
-            qsum += (double)q;
-          }
+        for (int e = 0; e < 2; ++e) {
+          const int64_t gx = tx0 + sp.x0 + i + e;
+          if (gy >= a.H || gx >= a.W) continue;
+          const float q = e == 0 ? (l1.x + l2.x) - 2.0f * l12.x + six_ln2
+                                 : (l1.y + l2.y) - 2.0f * l12.y + six_ln2;
+          if (a.q_map) a.q_map[gy * a.W + gx] = q;
+          qsum += (double)q;
         }
       }
     }
@@ -704,7 +707,7 @@ template <int R>
 size_t fwd_smem() {
   using T = WTile<R>;
   return T::P_FLOATS * sizeof(float) + (T::L * T::WROW + T::S_F2) * sizeof(float2) +
-         (kWT / 32) * sizeof(double);
+         (kWS / 32) * sizeof(double);
 }
 template <int R>
 size_t bwd_smem() {
@@ -732,15 +735,15 @@ int64_t tile_count(int64_t H, int64_t W) {
 }
 
 template <typename Kern>
-int launch_tiles(Kern kernel, size_t smem, const WsArgs& a, cudaStream_t s) {
+int launch_tiles(Kern kernel, size_t smem, const WsArgs& a, cudaStream_t s, int threads = kWT) {
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return ZINV_ERR_LAUNCH;
   }
   const int64_t tiles = tile_count(a.H, a.W);
-  const int64_t blocks = cover_blocks(tiles * kWT, kWT);
-  kernel<<<(unsigned)blocks, kWT, smem, s>>>(a);
+  const int64_t blocks = cover_blocks(tiles * threads, threads);
+  kernel<<<(unsigned)blocks, threads, smem, s>>>(a);
   return launch_status();
 }
 
@@ -795,9 +798,9 @@ extern "C" int wishart_stat_fwd(const float* s1, const float* s2, int64_t H, int
   a.q_map = q_map;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (win) {
-    case 3: rc = launch_tiles(k_wishart_fwd<1, false>, fwd_smem<1>(), a, st); break;
-    case 5: rc = launch_tiles(k_wishart_fwd<2, false>, fwd_smem<2>(), a, st); break;
-    default: rc = launch_tiles(k_wishart_fwd<3, false>, fwd_smem<3>(), a, st); break;
+    case 3: rc = launch_tiles(k_wishart_fwd<1, false>, fwd_smem<1>(), a, st, kWS); break;
+    case 5: rc = launch_tiles(k_wishart_fwd<2, false>, fwd_smem<2>(), a, st, kWS); break;
+    default: rc = launch_tiles(k_wishart_fwd<3, false>, fwd_smem<3>(), a, st, kWS); break;
   }
   if (rc != ZINV_OK) return rc;
   k_reduce_tiles<<<1, kRedThreads, 0, st>>>(a.partial, tile_count(H, W), 1, nullptr, d_loss, 1);
@@ -866,9 +869,9 @@ extern "C" int wishart_stat_fwd_save(const float* s1, const float* s2, int64_t H
   a.z_vec = aligned(z_saved, 16) && (W % 4) == 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (win) {
-    case 3: rc = launch_tiles(k_wishart_fwd<1, true>, fwd_smem<1>(), a, st); break;
-    case 5: rc = launch_tiles(k_wishart_fwd<2, true>, fwd_smem<2>(), a, st); break;
-    default: rc = launch_tiles(k_wishart_fwd<3, true>, fwd_smem<3>(), a, st); break;
+    case 3: rc = launch_tiles(k_wishart_fwd<1, true>, fwd_smem<1>(), a, st, kWS); break;
+    case 5: rc = launch_tiles(k_wishart_fwd<2, true>, fwd_smem<2>(), a, st, kWS); break;
+    default: rc = launch_tiles(k_wishart_fwd<3, true>, fwd_smem<3>(), a, st, kWS); break;
   }
   if (rc != ZINV_OK) return rc;
   k_reduce_tiles<<<1, kRedThreads, 0, st>>>(a.partial, tile_count(H, W), 1, nullptr, d_loss, 1);
@@ -983,9 +986,9 @@ extern "C" int wishart_stat_fwd_noalloc(const float* s1, const float* s2, int64_
   a.partial = scratch;  // every tile writes its own slot before the reduce reads it
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (win) {
-    case 3: rc = launch_tiles(k_wishart_fwd<1, false>, fwd_smem<1>(), a, st); break;
-    case 5: rc = launch_tiles(k_wishart_fwd<2, false>, fwd_smem<2>(), a, st); break;
-    default: rc = launch_tiles(k_wishart_fwd<3, false>, fwd_smem<3>(), a, st); break;
+    case 3: rc = launch_tiles(k_wishart_fwd<1, false>, fwd_smem<1>(), a, st, kWS); break;
+    case 5: rc = launch_tiles(k_wishart_fwd<2, false>, fwd_smem<2>(), a, st, kWS); break;
+    default: rc = launch_tiles(k_wishart_fwd<3, false>, fwd_smem<3>(), a, st, kWS); break;
   }
   if (rc != ZINV_OK) return rc;
   k_reduce_tiles<<<1, kRedThreads, 0, st>>>(a.partial, tiles, 1, nullptr, d_loss, 1);
