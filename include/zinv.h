@@ -300,7 +300,8 @@ int wishart_stat_bwd(const float* s1, const float* s2, int64_t H, int64_t W, int
  *   ws, ws_bytes  wishart_stat_fwd_save: as wishart_stat_fwd.
  *             wishart_stat_bwd_saved: at least
  *             wishart_bwd_saved_workspace_bytes(H, W, win) bytes, 8-byte
- *             aligned (per-tile partials, then the packed M of every pixel).
+ *             aligned (per-tile partials, then the packed M of every pixel;
+ *             16-byte aligned with W % 4 == 0 takes 16-byte copies of M).
  *   other arguments as wishart_stat_fwd / wishart_stat_bwd (the backward
  *   takes no weights: they entered through Z).
  * Images of more than 2^56 pixels are refused (ZINV_ERR_ARG), as are the

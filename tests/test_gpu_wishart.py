@@ -242,6 +242,26 @@ def test_saved_z_matches_recompute_and_oracle(zlib, orc, win, shape):
         assert np.all(np.abs(got - ref) <= gamma(K + 3) * scale)
 
 
+@pytest.mark.parametrize("offset", [0, 8])
+def test_saved_backward_workspace_alignment(zlib, offset):
+    """W % 4 == 0: a 16-byte aligned workspace takes 16-byte copies of M, one
+    8 bytes off takes 4-byte copies; both give the recomputing backward's bits."""
+    H, W = 52, 96
+    _, c1, c2 = pair(H, W)
+    s1, s2 = torch.from_numpy(c1).cuda(), torch.from_numpy(c2).cuda()
+    wd = torch.from_numpy(weights(7, 4)).cuda()
+    _, zs = zlib.wishart_stat_fwd_save(s1, s2, wd, 7)
+    need = zlib.wishart_bwd_saved_workspace_bytes(H, W, 7)
+    buf = torch.empty(need + 16, dtype=torch.uint8, device="cuda")
+    ws = buf[offset:offset + need]
+    assert ws.data_ptr() % 16 == offset
+    g = torch.tensor(0.5, dtype=torch.float64, device="cuda")
+    gw = zlib.wishart_stat_bwd(s1, s2, wd, 7, g)
+    gw2 = zlib.wishart_stat_bwd_saved(s1, s2, zs, 7, g, ws=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(gw, gw2)
+
+
 def test_saved_z_full_size_and_autograd(zlib):
     """The 4096 x 4096 pair in the benchmark's configuration: the saved path's
     loss and gradient are the recomputing path's bits, and WishartStat with
