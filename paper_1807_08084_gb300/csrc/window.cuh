@@ -226,9 +226,9 @@ __device__ __forceinline__ void window_all_paired(const float* P, const float2* 
 // Channel-split engine: two threads per 4 x 2 block of outputs, 128 per tile.
 // Lanes l and l ^ 8 of a warp share a block; half h = (l >> 3) & 1 sums
 // channel pairs 2h and 2h + 1 for both output rows and channel 8 for output
-// row h alone, so both halves issue the same FMAs (per tap: eight packed ones
-// and four scalar ones), and each quarter-warp reads one plane, as in the
-// paired engine.  Every accumulator adds its taps in the same order as the
+// row h alone, so both halves issue the same FMAs (per tap: 16 packed ones,
+// two channel pairs for eight outputs, and 4 scalar ones, channel 8 for four
+// outputs), and each quarter-warp reads one plane, as in the paired engine.  Every accumulator adds its taps in the same order as the
 // paired engine: the sums are the same bits.  After the sums the halves swap
 // the pairs of the other's row with one shuffle each, so half h holds all nine
 // channels of row h.  Twice the threads on the same shared memory doubles the
