@@ -379,7 +379,8 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
+    """The command line (also used to check the commands quoted in profiles/)."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -404,6 +405,11 @@ def main():
                     help="time the FP64 oracle on the host cores (rank 0, one GPU only)")
     ap.add_argument("--rows", type=int, default=16384,
                     help="image height (16384 = the full workload; smaller for profiling)")
+    return ap
+
+
+def main():
+    ap = build_parser()
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
